@@ -1,0 +1,220 @@
+"""Pin the oracle CTMRG to closed forms, exact special cases and invariants."""
+import os
+
+import numpy as np
+import pytest
+
+from oracle import ctmrg_ref as R
+from oracle import exact as X
+from oracle import elements as EL
+from paper_2112_13184_gb300 import inputs as I
+
+GOLDEN = os.path.join(os.path.dirname(__file__), "golden")
+
+
+def _ising_run(beta, chi=16, sweeps=60, seed=5):
+    A = I.ising_peps_tensor(beta)
+    As = [A] * 4
+    envs = I.random_env(chi, [2] * 4, seed=seed)
+    envs, n, delta = R.run(As, envs, chi, sweeps, tol=1e-13)
+    return As, envs
+
+
+@pytest.mark.parametrize("beta", [0.6, 0.3])
+def test_ising_onsager(beta):
+    """The Ising PEPS norm network is Z_Ising(K=beta): CTMRG must reproduce
+    Onsager's free energy and energy and the Onsager-Yang magnetisation."""
+    As, envs = _ising_run(beta)
+    sz = np.diag([1.0, -1.0])
+    m = np.array([R.expect(sz, R.rdm1(envs, As, i)) for i in range(4)])
+    zz = np.kron(sz, sz)
+    c = np.array([R.expect(zz, R.rdm2(envs, As, i, dx, dy)) for (i, dx, dy) in I.SQUARE_2X2_BONDS])
+    lk, sign = R.log_kappa_per_site(envs, As)
+    assert sign > 0
+    np.testing.assert_allclose(np.abs(m), X.yang_magnetisation(beta), atol=1e-10)
+    np.testing.assert_allclose(c, X.onsager_nn_correlation(beta), rtol=1e-10)
+    np.testing.assert_allclose(lk, X.onsager_log_z_per_site(beta), rtol=1e-12)
+
+
+def test_ising_magnetisation_is_uniform():
+    As, envs = _ising_run(0.6)
+    sz = np.diag([1.0, -1.0])
+    m = [R.expect(sz, R.rdm1(envs, As, i)) for i in range(4)]
+    assert np.ptp(m) < 1e-10
+
+
+def test_onsager_closed_forms_selfconsistent():
+    """u = -d(-beta f)/dK (numerical derivative of our quadrature) ties the
+    free-energy quadrature and the elliptic-integral energy together."""
+    for K in (0.3, 0.6):
+        h = 1e-5
+        du = -(X.onsager_log_z_per_site(K + h) - X.onsager_log_z_per_site(K - h)) / (2 * h)
+        assert abs(du - X.onsager_energy_per_site(K)) < 1e-8
+    # high-temperature limit: -beta f -> ln 2 ; low: -beta f -> 2K
+    assert abs(X.onsager_log_z_per_site(1e-6) - np.log(2)) < 1e-9
+    assert abs(X.onsager_log_z_per_site(3.0) - 6.0) < 1e-4
+
+
+@pytest.mark.parametrize("chi", [1, 3, 8])
+def test_neel_product_state_exact(chi):
+    """D=3 Neel state with no noise: a product state; any chi is exact."""
+    As = I.neel_tensors(2, 3, 0.0, seed=0)
+    envs = I.random_env(chi, [3] * 4, seed=1)
+    envs, _, _ = R.run(As, envs, chi, 4)
+    o = I.spin_ops(2)
+    for i in range(4):
+        x, y = i % 2, i // 2
+        expect = 0.5 if (x + y) % 2 == 0 else -0.5
+        assert abs(R.expect(o["Sz"], R.rdm1(envs, As, i)) - expect) < 1e-12
+    h = I.heisenberg_bond(2)
+    for (i, dx, dy) in I.SQUARE_2X2_BONDS:
+        assert abs(R.expect(h, R.rdm2(envs, As, i, dx, dy)) + 0.25) < 1e-12
+
+
+def test_hidden_rank1_bonds_product_state():
+    """A[s,l,u,r,d] = phi_s v_l w_u v'_r w'_d: rank-1 bonds hide a product
+    state; one- and two-site values are the product-state ones."""
+    rng = np.random.default_rng(11)
+    d, D, chi = 3, 3, 5
+    As, phis = [], []
+    for i in range(4):
+        phi = rng.standard_normal(d)
+        vs = [np.abs(rng.standard_normal(D)) + 0.1 for _ in range(4)]
+        As.append(np.einsum("s,l,u,r,d->slurd", phi, *vs))
+        phis.append(phi)
+    envs = I.random_env(chi, [D] * 4, seed=2)
+    envs, _, _ = R.run(As, envs, chi, 3)
+    op1 = I.spin_ops(3)["Sx"]
+    for i in range(4):
+        assert abs(R.expect(op1, R.rdm1(envs, As, i)) - X.product_expectation(phis[i], op1)) < 1e-11
+    op2 = I.blbq_bond(3)
+    for (i, dx, dy) in I.SQUARE_2X2_BONDS:
+        j = ((i % 2 + dx) % 2) + 2 * ((i // 2 + dy) % 2)
+        ref = X.product_expectation(np.kron(phis[i], phis[j]), op2)
+        assert abs(R.expect(op2, R.rdm2(envs, As, i, dx, dy)) - ref) < 1e-11
+
+
+@pytest.fixture(scope="module")
+def converged():
+    As = I.neel_tensors(2, 2, 0.3, seed=4)
+    chi = 12
+    envs = I.random_env(chi, [2] * 4, seed=9)
+    envs, n, delta = R.run(As, envs, chi, 80, tol=1e-12)
+    return As, envs, chi, delta
+
+
+def test_converges(converged):
+    assert converged[3] < 1e-11
+
+
+def test_rdm_invariants(converged):
+    As, envs, chi, _ = converged
+    for i in range(4):
+        r = R.rdm1(envs, As, i)
+        assert abs(np.trace(r) - 1) < 1e-14
+        assert np.max(np.abs(r - r.T)) < 1e-12 * np.max(np.abs(r))
+        assert np.min(np.linalg.eigvalsh(0.5 * (r + r.T))) > -1e-10
+    for (i, dx, dy) in I.SQUARE_2X2_BONDS:
+        r = R.rdm2(envs, As, i, dx, dy)
+        assert abs(np.trace(r) - 1) < 1e-14
+        assert np.max(np.abs(r - r.T)) < 1e-12 * np.max(np.abs(r))
+        assert np.min(np.linalg.eigvalsh(0.5 * (r + r.T))) > -1e-9
+        # partial trace over the target reproduces the one-site RDM up to truncation
+        r1 = np.einsum("ajbj->ab", r.reshape(2, 2, 2, 2))
+        assert np.max(np.abs(r1 - R.rdm1(envs, As, i))) < 1e-6
+
+
+def test_projector_identities(converged):
+    As, envs, chi, _ = converged
+    Qs = R.cut_corners(envs, As, 0, 1, 2, 2)
+    Pup, Pdn, s = R.projectors(*Qs, chi)
+    np.testing.assert_allclose(Pdn @ Pup, np.eye(chi), atol=1e-8)
+    Hu, Hd = R.half_systems(*Qs)
+    M = Hu.T @ Hd
+    U, S, Vt = np.linalg.svd(M)
+    lhs = Hu.T @ Pup @ Pdn @ Hd
+    rhs = (U[:, :chi] * S[:chi]) @ Vt[:chi]
+    assert np.max(np.abs(lhs - rhs)) < 1e-10 * S[0]
+
+
+def _observables(As, envs):
+    o = I.spin_ops(2)
+    h = I.heisenberg_bond(2)
+    one = [R.expect(o["Sz"], R.rdm1(envs, As, i)) for i in range(4)]
+    two = [R.expect(h, R.rdm2(envs, As, i, dx, dy)) for (i, dx, dy) in I.SQUARE_2X2_BONDS]
+    return np.array(one + two)
+
+
+def _gauge(As, G):
+    Gi = np.linalg.inv(G)
+    As2 = [a.copy() for a in As]
+    As2[0] = np.einsum("slurd,rk->slukd", As[0], G)
+    As2[1] = np.einsum("kl,slurd->skurd", Gi, As[1])
+    return As2
+
+
+@pytest.mark.parametrize("orthogonal", [True, False])
+def test_gauge_invariance(converged, orthogonal):
+    """G on the bond 0.r - 1.l leaves every observable unchanged.
+
+    An orthogonal G maps every half-system product to an orthogonally
+    equivalent one, so the truncation is the same and agreement is to
+    convergence; a general invertible G changes which directions are kept,
+    so agreement is only to the truncation error at this chi."""
+    As, envs, chi, _ = converged
+    rng = np.random.default_rng(3)
+    G = np.eye(2) + 0.4 * rng.standard_normal((2, 2))
+    if orthogonal:
+        G, _ = np.linalg.qr(G)
+    As2 = _gauge(As, G)
+    envs2 = I.random_env(chi, [2] * 4, seed=9)
+    envs2, _, delta = R.run(As2, envs2, chi, 120, tol=1e-12)
+    tol = 1e-9 if orthogonal else 1e-6
+    np.testing.assert_allclose(_observables(As2, envs2), _observables(As, envs), atol=tol)
+
+
+def test_lattice_rotation_swaps_bonds(converged):
+    """Rotating the tensors by 90 degrees maps horizontal bonds to vertical ones."""
+    As, envs, chi, _ = converged
+    e0 = I.random_env(chi, [2] * 4, seed=9)
+    _, As_r, _, _ = R.rotate_ccw(e0, As, 2, 2)
+    envs_r = I.random_env(chi, [2] * 4, seed=9)
+    envs_r, _, _ = R.run(As_r, envs_r, chi, 120, tol=1e-12)
+    h = I.heisenberg_bond(2)
+    # original horizontal bond (0 -> 1) is, after (x,y)->(-y,x), the vertical bond
+    # from image(1)=(0,1)=2 down to image(0)=0, i.e. source 0, (0,+1), target 2
+    # with sites swapped (image(0) is the bottom site)
+    e_h = R.expect(h, R.rdm2(envs, As, 0, 1, 0))
+    e_v = R.expect(h, R.rdm2(envs_r, As_r, 0, 0, 1))
+    assert abs(e_h - e_v) < 1e-8
+
+
+def test_product_state_energy_independent_of_chi():
+    As = I.neel_tensors(2, 2, 0.0, seed=0)
+    h = I.heisenberg_bond(2)
+    vals = []
+    for chi in (2, 5):
+        envs = I.random_env(chi, [2] * 4, seed=3)
+        envs, _, _ = R.run(As, envs, chi, 3)
+        vals.append(R.expect(h, R.rdm2(envs, As, 0, 1, 0)))
+    assert abs(vals[0] - vals[1]) < 1e-13
+
+
+def test_element_format_golden():
+    lines = EL.parse_elements("\n".join(l for l in open(os.path.join(GOLDEN, "heisenberg_elements.txt"))
+                                        if not l.startswith("#")))
+    op = EL.op_from_elements(2, 2, lines)
+    np.testing.assert_allclose(op, I.heisenberg_bond(2), atol=0)
+
+
+def test_element_format_orientation():
+    """<up down| S+_i S-_j |down up> = 1: before = (1, 0), after = (0, 1)."""
+    op = EL.op_from_elements(2, 2, [(1, 0, 0, 1, 1.0, 0.0)])
+    o = I.spin_ops(2)
+    np.testing.assert_array_equal(op, np.kron(o["Sp"], o["Sm"]))
+
+
+def test_bond_list_golden():
+    rows = [tuple(int(v) for v in l.split()) for l in open(os.path.join(GOLDEN, "square_2x2_bonds.txt"))
+            if l.strip() and not l.startswith("#")]
+    assert tuple(rows) == I.SQUARE_2X2_BONDS
