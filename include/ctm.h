@@ -1,0 +1,195 @@
+/*
+ * ctm.h -- C ABI of libctm: the CTMRG environment sweep of an iTPS on a 2x2
+ * unit cell and the reduced density matrices used to measure one- and
+ * two-site observables, on one NVIDIA GB300 (sm_103a).
+ *
+ * What the library computes (TeNeS, arXiv:2112.13184):
+ *   Sec. 2.1  an iTPS: one tensor A[s,l,u,r,d] per unit-cell site, physical
+ *             dimension d, four virtual legs of bond dimension D;
+ *   Sec. 2.2  its norm network, bra and ket merged into one layer of bond
+ *             dimension D^2, contracted by the corner-transfer-matrix
+ *             renormalisation group: four chi x chi corners C1..C4 and four
+ *             chi x D x D x chi edges T1..T4 per site, found by the
+ *             directional CTMRG for arbitrary unit cells with projectors
+ *             built without the QR step and a partial (randomised) SVD that
+ *             never forms the half-system matrix;
+ *   Sec. 5.3  the "observable" section: one-site and two-site (nearest
+ *             neighbour) operators, measured from reduced density matrices;
+ *   Sec. 5.2  the operator element format (before/after states, re, im).
+ *
+ * Conventions
+ *   - Sites i = x + 2y, x,y in {0,1}; y points up, (dx,dy) = (0,1) is the top
+ *     neighbour (Sec. 5.3, correlation displacement).
+ *   - A is C-order [s][l][u][r][d] (left, top, right, bottom; leg order of the
+ *     virtual_dim lists in Appendix A), FP64, d*D^4 doubles.
+ *   - Environment of a site, clockwise from the top-left corner, C-order:
+ *       which 0: C1[c_T4][c_T1]          1: T1[c_C1][k][k'][c_C2]
+ *             2: C2[c_T1][c_T2]          3: T2[c_C2][k][k'][c_C3]
+ *             4: C3[c_T2][c_T3]          5: T3[c_C3][k][k'][c_C4]
+ *             6: C4[c_T3][c_T4]          7: T4[c_C4][k][k'][c_C1]
+ *     k joins the ket tensor A, k' the bra tensor.  C: chi*chi doubles;
+ *     T: chi*D*D*chi doubles.
+ *   - Operators are real, row-major O[after][before]; two-site operators act
+ *     on the combined index (source*d + target) (Sec. 5.2).  Reduced density
+ *     matrices are rho[ket][bra] with trace 1, so <O> = Tr(O rho).
+ *
+ * Ownership and errors
+ *   - Every buffer passed in stays owned by the caller; the library copies in
+ *     and out.  Host pointers are plain host memory (pinned or not); device
+ *     pointers must be device-resident FP64 arrays of the stated size.
+ *   - All work of a handle is ordered on the CUDA stream given at creation.
+ *     Calls that return values to host memory synchronise that stream.
+ *   - Functions return a ctm_status; negative values are errors, and
+ *     ctm_last_error(h) gives a message.  No C++ exception crosses the ABI.
+ *   - A handle is not thread-safe; use one handle per host thread.
+ */
+#ifndef CTM_H
+#define CTM_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct ctm_ctx* ctm_handle;
+
+typedef enum {
+    CTM_OK = 0,
+    CTM_NOT_CONVERGED = 1,   /* ctm_run hit max_sweeps; results are still valid */
+    CTM_ERR_ARG = -1,        /* bad argument (size, index, null pointer)          */
+    CTM_ERR_OOM = -2,        /* device allocation failed                          */
+    CTM_ERR_CUDA = -3,       /* a CUDA call failed                                */
+    CTM_ERR_NONFINITE = -4,  /* NaN/Inf appeared in the environment               */
+    CTM_ERR_TIMEOUT = -5,    /* a bounded device wait gave up                     */
+    CTM_ERR_STATE = -6       /* call out of order (e.g. no tensors set)           */
+} ctm_status;
+
+typedef enum {
+    CTM_FP64 = 0,        /* every contraction in FP64 (CUDA-core DFMA)             */
+    CTM_OZAKI_BF16 = 1   /* contractions as exact BF16 slice products on the
+                            tensor cores (tcgen05), emulating FP64; QR, SVD and
+                            normalisation stay FP64                               */
+} ctm_precision;
+
+typedef struct {
+    int chi;                /* corner bond dimension chi (Sec. 2.2)              */
+    int max_sweeps;         /* ctm_run: sweep cap                                 */
+    double tol;             /* ctm_run: stop when the corner-spectrum change < tol */
+    int precision;          /* ctm_precision                                       */
+    int ozaki_slices;       /* CTM_OZAKI_BF16: slices per operand, 3..6            */
+    int rsvd_oversample;    /* randomised SVD: k = min(chi + p, chi*D*D)           */
+    int rsvd_power_iters;   /* randomised SVD: power iterations q                  */
+    double sv_cutoff_rel;   /* S^{-1/2} := 0 for s < cutoff * s_0                  */
+    uint64_t seed;          /* counter-based RNG seed for the rSVD test matrices   */
+    int exact_svd_max_n;    /* N = chi*D*D <= this: k = N, the range finder spans
+                               everything and the truncated SVD is exact           */
+} ctm_options;
+
+/* Defaults: chi=16, max_sweeps=100, tol=1e-10, FP64, 4 slices,
+ * p=max(8,chi/8) (when rsvd_oversample<=0), q=2, cutoff 1e-12, seed 0,
+ * exact_svd_max_n=256. */
+ctm_status ctm_default_options(ctm_options* opt);
+
+/* Device bytes a handle of this shape allocates (workspace included). */
+ctm_status ctm_footprint_bytes(int d, int D, const ctm_options* opt, size_t* bytes);
+
+/* Create a handle for a 2x2 cell with physical dim d and bond dim D on
+ * the current CUDA device.  stream: a cudaStream_t, or NULL to create one
+ * owned by the handle.  Allocates all device memory up front. */
+ctm_status ctm_create(int d, int D, const ctm_options* opt, void* stream, ctm_handle* out);
+ctm_status ctm_destroy(ctm_handle h);
+
+/* Copy in the site tensor A of site i (d*D^4 doubles, C-order [s,l,u,r,d]). */
+ctm_status ctm_set_tensor(ctm_handle h, int site, const double* A, int on_device);
+
+/* Copy in / out one environment tensor (which = 0..7, see above). */
+ctm_status ctm_set_env(ctm_handle h, int site, int which, const double* t, int on_device);
+ctm_status ctm_get_env(ctm_handle h, int site, int which, double* t, int on_device);
+
+/* n CTMRG sweeps (left, top, right, bottom moves; Sec. 2.2). */
+ctm_status ctm_sweep(ctm_handle h, int n);
+
+/* Sweeps until the normalised corner spectra change by less than opt.tol
+ * (max-abs over the 16 corners) or opt.max_sweeps is reached.  Either
+ * output pointer may be NULL.  Returns CTM_NOT_CONVERGED at the cap. */
+ctm_status ctm_run(ctm_handle h, int* sweeps_done, double* last_delta);
+
+/* Normalised singular values (sum 1) of every corner: out[site][corner][chi]. */
+ctm_status ctm_corner_spectra(ctm_handle h, double* out_host);
+
+/* Reduced density matrices (host outputs, trace 1, rho[ket][bra]).
+ * rdm2: target = site + (dx,dy), |dx|+|dy| == 1; rho over (source, target). */
+ctm_status ctm_rdm1(ctm_handle h, int site, double* rho_host);
+ctm_status ctm_rdm2(ctm_handle h, int site, int dx, int dy, double* rho_host);
+
+/* <O> = Tr(O rho) for a d*d (one-site) or d^2*d^2 (two-site) host operator. */
+ctm_status ctm_measure1(ctm_handle h, int site, const double* op, double* value);
+ctm_status ctm_measure2(ctm_handle h, int site, int dx, int dy, const double* op, double* value);
+
+/* Operator from the element format of Sec. 5.2: n lines of
+ * (i_before, j_before, i_after, j_after) in idx[4n] and real parts re[n];
+ * writes the (d0*d1)^2 row-major matrix O[after][before] (zeroed first).
+ * A one-site operator uses d1 = 1 and j = 0. */
+ctm_status ctm_op_from_elements(int d0, int d1, int n, const int* idx, const double* re,
+                                double* op_out);
+
+const char* ctm_last_error(ctm_handle h);
+const char* ctm_status_string(ctm_status s);
+
+/* Instrumentation (no counterpart in the paper).  When enabled, every
+ * contraction, permutation, QR and SVD of the handle is bracketed by CUDA
+ * events on its stream; ctm_profile_read returns the accumulated device
+ * time per class together with the algorithmic FLOPs (2MNK per GEMM) and
+ * bytes (read + write per permutation) of the calls timed.  Classes:
+ * 0 GEMM, 1 permute, 2 QR, 3 SVD.  reset != 0 zeroes the counters. */
+typedef struct {
+    double ms[4];
+    double flops[4];
+    double bytes[4];
+    long long calls[4];
+} ctm_profile_data;
+ctm_status ctm_profile_enable(ctm_handle h, int on);
+ctm_status ctm_profile_read(ctm_handle h, ctm_profile_data* out, int reset);
+
+/* Number of CUDA kernels libctm has launched in this process (all handles
+ * and kernel-level calls); cudaMemset/cudaMemcpy are not counted. */
+long long ctm_kernel_launches(void);
+
+/* ------------------------------------------------------------------------
+ * Kernel-level entry points.  All pointers are device pointers, work is
+ * ordered on `stream` (cudaStream_t, NULL = legacy default stream), nothing
+ * is synchronised, and no memory is allocated unless stated.  They are the
+ * building blocks of the sweep, exported for per-kernel parity tests.
+ * ------------------------------------------------------------------------ */
+
+/* C[M,N] = alpha * op(A) op(B) + beta * C, row-major, FP64.  op(X) = X or
+ * X^T (trans != 0).  lda/ldb/ldc are row strides of the stored arrays. */
+ctm_status ctm_dgemm(int transA, int transB, int M, int N, int K, double alpha,
+                     const double* A, int lda, const double* B, int ldb, double beta,
+                     double* C, int ldc, void* stream);
+
+/* dst = src with axes permuted: dst dims are dims[perm[0..ndim-1]] and
+ * dst[i_0..] = src[j] with j_{perm[a]} = i_a.  ndim <= 8, FP64. */
+ctm_status ctm_permute(const double* src, double* dst, int ndim, const int* dims,
+                       const int* perm, void* stream);
+
+/* Thin Householder QR of Y (N x k row-major, N >= k): Q (N x k) with
+ * orthonormal columns and upper-triangular R (k x k, diagonal >= 0), Y=QR.
+ * Y is not modified.  ws: workspace of ctm_qr_workspace_bytes(N,k) bytes. */
+size_t ctm_qr_workspace_bytes(int N, int k);
+ctm_status ctm_qr(const double* Y, int N, int k, double* Q, double* R, void* ws, void* stream);
+
+/* SVD of a small square G (k x k row-major, k <= 1024) by one-sided Jacobi:
+ * G = U diag(S) V^T, S descending, U and V k x k row-major.  Columns of U
+ * with S = 0 are zero.  ws: ctm_svd_workspace_bytes(k) bytes. */
+size_t ctm_svd_workspace_bytes(int k);
+ctm_status ctm_svd(const double* G, int k, double* U, double* S, double* V, void* ws,
+                   void* stream);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* CTM_H */

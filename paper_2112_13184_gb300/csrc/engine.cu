@@ -1,0 +1,849 @@
+// CTMRG engine and C ABI (include/ctm.h).
+//
+// The sweep (Sec. 2.2) is built from one routine: the enlarged corner
+//   E(C, T, T', A)[(a,d,d'), (b,r,r')] = sum C[g,h] T[h,u,u',b] T'[a,l,l',g]
+//                                        A[s,l,u,r,d] A[s,l',u',r',d'],
+// the upper-left corner of a site.  The other three corners are the same
+// routine on the lattice rotated by 90, 180, 270 degrees counter-clockwise:
+// corner c of a site is E(C_c, T_c, T_{c-1}, rot^c A), rot(A)[s,l,u,r,d] =
+// A[s,d,l,u,r], with the corners/edges numbered clockwise (C1 T1 C2 T2 ...).
+// A left move on the frame rotated m times is the move in direction m.
+//
+// Projectors of a cut (QR-free, Sec. 2.2): with H_u = Q_ul Q_ur, H_d = Q_bl Q_br
+// and M = H_u^T H_d, the top-chi SVD M ~ U S V^T is taken by a randomised
+// range finder (Halko et al.) that only applies M and M^T as chains of four
+// corner products -- M is never formed:
+//   M X   = E_ur^T E_ul^T E_bl^T E_br^T X,   M^T X = E_br E_bl E_ul E_ur X,
+//   P_up  = E_bl^T E_br^T V S^{-1/2},        P_dn^T = E_ul E_ur U S^{-1/2}.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <new>
+#include <string>
+#include <vector>
+
+#include "internal.h"
+
+using namespace ctm;
+
+namespace {
+
+enum { C1 = 0, T1 = 1, C2 = 2, T2 = 3, C3 = 4, T3 = 5, C4 = 6, T4 = 7 };
+inline int Cw(int c) { return 2 * (c & 3); }
+inline int Tw(int c) { return 2 * (c & 3) + 1; }
+
+// frame m: site at frame position p -> original site index
+struct FrameMaps {
+    int m[4][4];
+    FrameMaps() {
+        int cur[4] = {0, 1, 2, 3};
+        for (int f = 0; f < 4; ++f) {
+            for (int p = 0; p < 4; ++p) m[f][p] = cur[p];
+            int nxt[4];
+            for (int y = 0; y < 2; ++y)
+                for (int x = 0; x < 2; ++x) {
+                    const int i = x + 2 * y;
+                    const int j = ((2 - y) % 2) + 2 * (x % 2);
+                    nxt[j] = cur[i];
+                }
+            std::memcpy(cur, nxt, sizeof(cur));
+        }
+    }
+    int site(int f, int x, int y) const { return m[f & 3][((x % 2 + 2) % 2) + 2 * ((y % 2 + 2) % 2)]; }
+};
+const FrameMaps FM;
+
+}  // namespace
+
+struct ctm_ctx {
+    int d = 0, D = 0, chi = 0, N = 0, k = 0, q = 0;
+    ctm_options opt{};
+    cudaStream_t stream = nullptr;
+    bool own_stream = false;
+    std::string err;
+    bool have_A[4] = {false, false, false, false};
+    unsigned env_set = 0;  // bit (site*8 + which)
+    uint64_t rng_counter = 0;
+
+    std::vector<void*> allocs;
+    double* A[4][4] = {};     // [site][rotation]  [s,l,u,r,d]
+    double* Alu[4][4] = {};   // [site][rotation]  [l,u,s,r,d]
+    double* env[4][8] = {};   // [site][which]
+    // scratch
+    double *X1 = nullptr, *S1 = nullptr, *S2 = nullptr, *S3 = nullptr;
+    double* E[4] = {};        // ul, ur, br, bl of the current cut
+    double *Pup[2] = {}, *PdnT[2] = {};
+    double *Om = nullptr, *Yb = nullptr, *Zb = nullptr, *Qm = nullptr, *Qm2 = nullptr, *Qb = nullptr;
+    double *Rb = nullptr, *G = nullptr, *Us = nullptr, *Ws = nullptr, *Sv = nullptr, *inv = nullptr;
+    double *Uc = nullptr, *Vc = nullptr, *t1 = nullptr, *t2 = nullptr;
+    double *newC1 = nullptr, *newC4 = nullptr, *newT4 = nullptr, *tmpT = nullptr;
+    double *Lh = nullptr, *Rh = nullptr, *rho = nullptr, *spec = nullptr, *corners = nullptr;
+    double* splitk = nullptr;  // split-K partial sums
+    size_t splitk_n = 0;
+    // optional per-class device timing (ctm_profile_*)
+    bool prof = false;
+    std::vector<cudaEvent_t> ev_pool;
+    size_t ev_used = 0;
+    struct Rec { int cls; size_t ev; double flops, bytes; };
+    std::vector<Rec> recs;
+    double p_ms[4] = {0, 0, 0, 0}, p_flops[4] = {0, 0, 0, 0}, p_bytes[4] = {0, 0, 0, 0};
+    long long p_calls[4] = {0, 0, 0, 0};
+    void* qr_ws = nullptr;
+    void* svd_ws = nullptr;
+    void* sval_ws = nullptr;
+    unsigned long long* maxbits = nullptr;
+    int* flag = nullptr;
+};
+
+namespace {
+
+#define CK(expr)                                                                   \
+    do {                                                                           \
+        cudaError_t e_ = (expr);                                                   \
+        if (e_ != cudaSuccess) {                                                   \
+            h->err = std::string(#expr) + ": " + cudaGetErrorString(e_);           \
+            return CTM_ERR_CUDA;                                                   \
+        }                                                                          \
+    } while (0)
+#define CKS(expr)                           \
+    do {                                    \
+        ctm_status s_ = (expr);             \
+        if (s_ != CTM_OK) return s_;        \
+    } while (0)
+
+struct Sizes {
+    size_t A, C, T, NN, Nk, Nchi, kk, open;
+};
+
+Sizes sizes_of(int d, int D, int chi, int k) {
+    Sizes z;
+    const size_t N = (size_t)chi * D * D;
+    z.A = (size_t)d * D * D * D * D;
+    z.C = (size_t)chi * chi;
+    z.T = (size_t)chi * D * D * chi;
+    z.NN = N * N;
+    z.Nk = N * k;
+    z.Nchi = N * chi;
+    z.kk = (size_t)k * k;
+    z.open = (size_t)d * d * N * N;
+    return z;
+}
+
+int rsvd_k(int N, int chi, const ctm_options& o) {
+    if (N <= o.exact_svd_max_n) return N;
+    int p = o.rsvd_oversample > 0 ? o.rsvd_oversample : std::max(8, chi / 8);
+    return std::min(N, chi + p);
+}
+
+size_t footprint(int d, int D, const ctm_options& o) {
+    const int chi = o.chi;
+    const int N = chi * D * D;
+    const int k = rsvd_k(N, chi, o);
+    Sizes z = sizes_of(d, D, chi, k);
+    size_t dbl = 0;
+    dbl += 32 * z.A;                 // A, Alu for 4 sites x 4 rotations
+    dbl += 16 * z.C + 16 * z.T;      // environments
+    dbl += z.T;                      // X1
+    dbl += 2 * z.open + (size_t)d * z.NN;  // S1, S3 (open RDM size), S2
+    dbl += 4 * z.NN;                 // E
+    dbl += 4 * z.Nchi;               // Pup, PdnT
+    dbl += 6 * z.Nk;                 // Om, Y, Z, Qm, Qm2, Qb
+    dbl += 4 * z.kk + 2 * (size_t)k; // Rb, G, Us, Ws, Sv, inv
+    dbl += 4 * z.Nchi;               // Uc, Vc, t1, t2
+    dbl += 2 * z.C + 2 * z.T;        // newC1, newC4, newT4, tmpT
+    dbl += 2 * z.Nchi * d * d;       // Lh, Rh
+    dbl += std::max<size_t>(64 * 64, (size_t)d * d * d * d) + 2 * 16 * z.C;  // rho, spectra, corners
+    dbl += (size_t)1 << 24;          // split-K partials
+    size_t bytes = dbl * sizeof(double);
+    bytes += qr_ws_bytes(N, k) + svd_ws_bytes(k) + svals_ws_bytes(chi, 16);
+    bytes += 64 * sizeof(unsigned long long) + 64 + 64 * 256;
+    return bytes;
+}
+
+ctm_status alloc(ctm_ctx* h, void** p, size_t bytes) {
+    cudaError_t e = cudaMalloc(p, bytes ? bytes : 8);
+    if (e != cudaSuccess) {
+        h->err = std::string("cudaMalloc: ") + cudaGetErrorString(e);
+        cudaGetLastError();
+        return CTM_ERR_OOM;
+    }
+    h->allocs.push_back(*p);
+    return CTM_OK;
+}
+template <class Tp>
+ctm_status allocd(ctm_ctx* h, Tp** p, size_t n) {
+    return alloc(h, (void**)p, n * sizeof(Tp));
+}
+
+// ----------------------------------------------------------------------------
+// per-class device timing: an event pair around each call when enabled
+// ----------------------------------------------------------------------------
+enum { P_GEMM = 0, P_PERM = 1, P_QR = 2, P_SVD = 3 };
+constexpr size_t NO_EV = ~(size_t)0;
+
+size_t prof_begin(ctm_ctx* h) {
+    if (!h->prof) return NO_EV;
+    while (h->ev_pool.size() < h->ev_used + 2) {
+        cudaEvent_t e;
+        if (cudaEventCreate(&e) != cudaSuccess) return NO_EV;
+        h->ev_pool.push_back(e);
+    }
+    const size_t i = h->ev_used;
+    cudaEventRecord(h->ev_pool[i], h->stream);
+    h->ev_used += 2;
+    return i;
+}
+void prof_end(ctm_ctx* h, size_t i, int cls, double flops, double bytes) {
+    if (i == NO_EV) return;
+    cudaEventRecord(h->ev_pool[i + 1], h->stream);
+    h->recs.push_back({cls, i, flops, bytes});
+}
+void prof_collect(ctm_ctx* h) {
+    if (h->recs.empty()) return;
+    cudaStreamSynchronize(h->stream);
+    for (const auto& r : h->recs) {
+        float ms = 0.f;
+        cudaEventElapsedTime(&ms, h->ev_pool[r.ev], h->ev_pool[r.ev + 1]);
+        h->p_ms[r.cls] += ms;
+        h->p_flops[r.cls] += r.flops;
+        h->p_bytes[r.cls] += r.bytes;
+        h->p_calls[r.cls] += 1;
+    }
+    h->recs.clear();
+    h->ev_used = 0;
+}
+
+// ----------------------------------------------------------------------------
+// contractions
+// ----------------------------------------------------------------------------
+ctm_status gemm(ctm_ctx* h, bool tA, bool tB, int M, int N, int K, const double* A, int lda,
+                const double* B, int ldb, double* C, int ldc, double beta = 0.0) {
+    const size_t ev = prof_begin(h);
+    CK(ctm::dgemm(tA, tB, M, N, K, 1.0, A, lda, B, ldb, beta, C, ldc, h->stream, h->splitk, h->splitk_n));
+    prof_end(h, ev, P_GEMM, 2.0 * M * N * K, 8.0 * ((double)M * K + (double)K * N + (double)M * N));
+    return CTM_OK;
+}
+ctm_status perm(ctm_ctx* h, const double* src, double* dst, std::initializer_list<int> dims,
+                std::initializer_list<int> p) {
+    std::vector<int> dv(dims), pv(p);
+    double n = 1;
+    for (int v : dv) n *= v;
+    const size_t ev = prof_begin(h);
+    CK(ctm::permute(src, dst, (int)dv.size(), dv.data(), pv.data(), h->stream));
+    prof_end(h, ev, P_PERM, 0.0, 16.0 * n);
+    return CTM_OK;
+}
+ctm_status qr_(ctm_ctx* h, const double* Y, double* Q, double* R) {
+    const size_t ev = prof_begin(h);
+    CK(ctm::qr(Y, h->N, h->k, Q, R, h->qr_ws, h->stream));
+    prof_end(h, ev, P_QR, 4.0 * h->N * (double)h->k * h->k, 0.0);
+    return CTM_OK;
+}
+ctm_status svd_(ctm_ctx* h) {
+    const size_t ev = prof_begin(h);
+    CK(ctm::svd(h->G, h->k, h->Us, h->Sv, h->Ws, h->svd_ws, h->stream));
+    prof_end(h, ev, P_SVD, 0.0, 0.0);
+    return CTM_OK;
+}
+
+// X1[g,u,u',b] (chi x D x D x chi), Tp[a,l,l',g], A / Alu of one rotation.
+// closed: out[(a,d,d'), (b,r,r')] (N x N).
+// open:   out[a,b,r,d,s,t,r',d'] (d^2 N^2), physical indices left open.
+ctm_status corner_core(ctm_ctx* h, const double* X1, const double* Tp, const double* A,
+                       const double* Alu, double* out, bool open) {
+    const int chi = h->chi, D = h->D, d = h->d, N = h->N;
+    const int D2 = D * D;
+    // X2[(a,l,l'), (u,u',b)] = Tp[(a,l,l'), g] X1[g, (u,u',b)]
+    CKS(gemm(h, false, false, N, N, chi, Tp, chi, X1, N, h->S1, N));
+    // -> [a,l',u',b,l,u]
+    CKS(perm(h, h->S1, h->S2, {chi, D, D, D, D, chi}, {0, 2, 4, 5, 1, 3}));
+    // X3[(a,l',u',b), (s,r,d)] = X2p[(a,l',u',b), (l,u)] Alu[(l,u), (s,r,d)]
+    const int M3 = chi * chi * D2;
+    CKS(gemm(h, false, false, M3, d * D2, D2, h->S2, D2, Alu, d * D2, h->S1, d * D2));
+    // -> [a,b,r,d,s,l',u']
+    CKS(perm(h, h->S1, h->S2, {chi, D, D, chi, d, D, D}, {0, 3, 5, 6, 4, 1, 2}));
+    if (!open) {
+        // X4[(a,b,r,d), (r',d')] = X3p[(a,b,r,d), (s,l',u')] A[(s,l',u'), (r',d')]
+        CKS(gemm(h, false, false, M3, D2, d * D2, h->S2, d * D2, A, D2, h->S1, D2));
+        // -> [a,d,d',b,r,r']
+        CKS(perm(h, h->S1, out, {chi, chi, D, D, D, D}, {0, 3, 5, 1, 2, 4}));
+    } else {
+        // X4o[(a,b,r,d,s), (t,r',d')] = X3p[(a,b,r,d,s), (l',u')] Alu[(l',u'), (t,r',d')]
+        CKS(gemm(h, false, false, M3 * d, d * D2, D2, h->S2, D2, Alu, d * D2, out, d * D2));
+    }
+    return CTM_OK;
+}
+
+// corner c (0..3 = C1..C4 position) of site i as an N x N matrix.
+ctm_status enlarged_corner(ctm_ctx* h, int i, int c, double* out) {
+    const int chi = h->chi, N = h->N;
+    CKS(gemm(h, false, false, chi, N, chi, h->env[i][Cw(c)], chi, h->env[i][Tw(c)], N, h->X1, N));
+    return corner_core(h, h->X1, h->env[i][Tw(c + 3)], h->A[i][c & 3], h->Alu[i][c & 3], out, false);
+}
+
+// ----------------------------------------------------------------------------
+// randomised SVD of M = H_u^T H_d and the projectors of one cut
+// ----------------------------------------------------------------------------
+ctm_status applyM(ctm_ctx* h, const double* X, double* out, int cols) {
+    const int N = h->N;
+    CKS(gemm(h, true, false, N, cols, N, h->E[2], N, X, cols, h->t1, cols));      // E_br^T X
+    CKS(gemm(h, true, false, N, cols, N, h->E[3], N, h->t1, cols, h->t2, cols));  // E_bl^T
+    CKS(gemm(h, true, false, N, cols, N, h->E[0], N, h->t2, cols, h->t1, cols));  // E_ul^T
+    CKS(gemm(h, true, false, N, cols, N, h->E[1], N, h->t1, cols, out, cols));    // E_ur^T
+    return CTM_OK;
+}
+ctm_status applyMT(ctm_ctx* h, const double* X, double* out, int cols) {
+    const int N = h->N;
+    CKS(gemm(h, false, false, N, cols, N, h->E[1], N, X, cols, h->t1, cols));      // E_ur X
+    CKS(gemm(h, false, false, N, cols, N, h->E[0], N, h->t1, cols, h->t2, cols));  // E_ul
+    CKS(gemm(h, false, false, N, cols, N, h->E[3], N, h->t2, cols, h->t1, cols));  // E_bl
+    CKS(gemm(h, false, false, N, cols, N, h->E[2], N, h->t1, cols, out, cols));    // E_br
+    return CTM_OK;
+}
+
+ctm_status projectors(ctm_ctx* h, int slot) {
+    const int N = h->N, k = h->k, chi = h->chi;
+    const int q = (k == N) ? 0 : h->q;
+    CK(ctm::rng_normal(h->Om, (size_t)N * k, h->opt.seed, h->rng_counter++, h->stream));
+    CKS(applyM(h, h->Om, h->Yb, k));
+    CKS(qr_(h, h->Yb, h->Qm, h->Rb));
+    for (int it = 0; it < q; ++it) {
+        CKS(applyMT(h, h->Qm, h->Zb, k));
+        CKS(qr_(h, h->Zb, h->Qm2, h->Rb));
+        CKS(applyM(h, h->Qm2, h->Yb, k));
+        CKS(qr_(h, h->Yb, h->Qm, h->Rb));
+    }
+    // B^T = M^T Q = Q_b R_b  ->  B = R_b^T Q_b^T ; SVD(R_b^T) = U' S W^T
+    CKS(applyMT(h, h->Qm, h->Zb, k));
+    CKS(qr_(h, h->Zb, h->Qb, h->Rb));
+    CKS(perm(h, h->Rb, h->G, {k, k}, {1, 0}));
+    CKS(svd_(h));
+    // U = Q U'[:, :chi], V = Q_b W[:, :chi]
+    CKS(gemm(h, false, false, N, chi, k, h->Qm, k, h->Us, k, h->Uc, chi));
+    CKS(gemm(h, false, false, N, chi, k, h->Qb, k, h->Ws, k, h->Vc, chi));
+    CK(ctm::inv_sqrt_cut(h->Sv, h->inv, chi, h->opt.sv_cutoff_rel, h->stream));
+    // P_up = E_bl^T (E_br^T V) S^-1/2 ; P_dn^T = E_ul (E_ur U) S^-1/2
+    CKS(gemm(h, true, false, N, chi, N, h->E[2], N, h->Vc, chi, h->t1, chi));
+    CKS(gemm(h, true, false, N, chi, N, h->E[3], N, h->t1, chi, h->Pup[slot], chi));
+    CK(ctm::scale_cols(h->Pup[slot], N, chi, chi, h->inv, h->stream));
+    CKS(gemm(h, false, false, N, chi, N, h->E[1], N, h->Uc, chi, h->t1, chi));
+    CKS(gemm(h, false, false, N, chi, N, h->E[0], N, h->t1, chi, h->PdnT[slot], chi));
+    CK(ctm::scale_cols(h->PdnT[slot], N, chi, chi, h->inv, h->stream));
+    return CTM_OK;
+}
+
+ctm_status normalise_into(ctm_ctx* h, const double* src, double* dst, size_t n, int slot) {
+    CK(cudaMemsetAsync(h->maxbits + slot, 0, sizeof(unsigned long long), h->stream));
+    CK(ctm::maxabs(src, n, h->maxbits + slot, h->stream));
+    CK(cudaMemcpyAsync(dst, src, n * sizeof(double), cudaMemcpyDeviceToDevice, h->stream));
+    CK(ctm::scale_by_max(dst, n, h->maxbits + slot, h->flag, h->stream));
+    return CTM_OK;
+}
+
+// absorb column x of frame m into the left boundary of column x+1
+ctm_status left_move(ctm_ctx* h, int m, int x) {
+    const int chi = h->chi, N = h->N, D = h->D;
+    for (int y = 0; y < 2; ++y) {
+        const int tl = FM.site(m, x, y + 1), tr = FM.site(m, x + 1, y + 1);
+        const int br = FM.site(m, x + 1, y), bl = FM.site(m, x, y);
+        CKS(enlarged_corner(h, tl, m + 0, h->E[0]));
+        CKS(enlarged_corner(h, tr, m + 1, h->E[1]));
+        CKS(enlarged_corner(h, br, m + 2, h->E[2]));
+        CKS(enlarged_corner(h, bl, m + 3, h->E[3]));
+        CKS(projectors(h, y));
+    }
+    for (int y = 0; y < 2; ++y) {
+        const int i = FM.site(m, x, y), j = FM.site(m, x + 1, y);
+        const int ym = (y + 1) % 2;  // cut between rows y-1 and y
+        double** e = h->env[i];
+        // C1' = P_up(y)^T (C1 T1)
+        CKS(gemm(h, false, false, chi, N, chi, e[Cw(m)], chi, e[Tw(m)], N, h->X1, N));
+        CKS(gemm(h, true, false, chi, chi, N, h->Pup[y], chi, h->X1, chi, h->newC1, chi));
+        // T4' = P_up(y-1)^T core(P_dn(y)^T, T4, A)   -> [c1, c2, r, r'] -> [c1, r, r', c2]
+        CKS(corner_core(h, h->PdnT[y], e[Tw(m + 3)], h->A[i][m & 3], h->Alu[i][m & 3], h->E[0], false));
+        CKS(gemm(h, true, false, chi, N, N, h->Pup[ym], chi, h->E[0], N, h->tmpT, N));
+        CKS(perm(h, h->tmpT, h->newT4, {chi, chi, D, D}, {0, 2, 3, 1}));
+        // C4' = (C4 T3)^T P_dn(y-1)^T :  Z[z,d,d',g] = T3[(z,d,d'),h] C4[h,g] -> [z,g,d,d']
+        CKS(gemm(h, false, false, N, chi, chi, e[Tw(m + 2)], chi, e[Cw(m + 3)], chi, h->t1, chi));
+        CKS(perm(h, h->t1, h->t2, {chi, D, D, chi}, {0, 3, 1, 2}));
+        CKS(gemm(h, false, false, chi, chi, N, h->t2, N, h->PdnT[ym], chi, h->newC4, chi));
+        double** ej = h->env[j];
+        CKS(normalise_into(h, h->newC1, ej[Cw(m)], (size_t)chi * chi, 0));
+        CKS(normalise_into(h, h->newT4, ej[Tw(m + 3)], (size_t)chi * N, 1));
+        CKS(normalise_into(h, h->newC4, ej[Cw(m + 3)], (size_t)chi * chi, 2));
+    }
+    return CTM_OK;
+}
+
+ctm_status one_sweep(ctm_ctx* h) {
+    for (int m = 0; m < 4; ++m)
+        for (int x = 0; x < 2; ++x) CKS(left_move(h, m, x));
+    return CTM_OK;
+}
+
+ctm_status check_ready(ctm_ctx* h) {
+    for (int i = 0; i < 4; ++i)
+        if (!h->have_A[i]) {
+            h->err = "site tensors not set";
+            return CTM_ERR_STATE;
+        }
+    if (h->env_set != 0xffffffffu) {
+        h->err = "environment not set (all 8 tensors of all 4 sites)";
+        return CTM_ERR_STATE;
+    }
+    return CTM_OK;
+}
+
+ctm_status read_flag(ctm_ctx* h) {
+    int f = 0;
+    CK(cudaMemcpyAsync(&f, h->flag, sizeof(int), cudaMemcpyDeviceToHost, h->stream));
+    CK(cudaStreamSynchronize(h->stream));
+    if (f) {
+        h->err = "non-finite environment";
+        return CTM_ERR_NONFINITE;
+    }
+    return CTM_OK;
+}
+
+ctm_status spectra(ctm_ctx* h, std::vector<double>& out) {
+    const int chi = h->chi;
+    const size_t C = (size_t)chi * chi;
+    for (int i = 0; i < 4; ++i)
+        for (int c = 0; c < 4; ++c)
+            CK(cudaMemcpyAsync(h->corners + (i * 4 + c) * C, h->env[i][Cw(c)], C * sizeof(double),
+                               cudaMemcpyDeviceToDevice, h->stream));
+    CK(ctm::svals_normalised(h->corners, chi, 16, h->spec, h->sval_ws, h->stream));
+    out.resize(16 * (size_t)chi);
+    CK(cudaMemcpyAsync(out.data(), h->spec, out.size() * sizeof(double), cudaMemcpyDeviceToHost, h->stream));
+    CK(cudaStreamSynchronize(h->stream));
+    return CTM_OK;
+}
+
+// ----------------------------------------------------------------------------
+// reduced density matrices
+// ----------------------------------------------------------------------------
+ctm_status rdm1_dev(ctm_ctx* h, int i, std::vector<double>& rho) {
+    const int chi = h->chi, D = h->D, d = h->d, N = h->N;
+    double** e = h->env[i];
+    CKS(gemm(h, false, false, chi, N, chi, e[C1], chi, e[T1], N, h->X1, N));
+    CKS(corner_core(h, h->X1, e[T4], h->A[i][0], h->Alu[i][0], h->S3, true));  // [a,b,r,d,s,t,r',d']
+    // ring C2 T2 C3 T3 C4 -> [b,r,r',d,d',a]
+    CKS(gemm(h, false, false, chi, N, chi, e[C2], chi, e[T2], N, h->t1, N));          // [b,r,r',e]
+    CKS(gemm(h, false, false, N, chi, chi, h->t1, chi, e[C3], chi, h->t2, chi));      // [b,r,r',f]
+    CKS(gemm(h, false, false, N, N, chi, h->t2, chi, e[T3], N, h->E[0], N));          // [b,r,r',d,d',g]
+    CKS(gemm(h, false, false, N * D * D, chi, chi, h->E[0], chi, e[C4], chi, h->E[1], chi));  // [..,a]
+    CKS(perm(h, h->E[1], h->E[2], {chi, D, D, D, D, chi}, {5, 0, 1, 3, 2, 4}));      // [a,b,r,d,r',d']
+    CKS(perm(h, h->S3, h->S1, {chi, chi, D, D, d, d, D, D}, {4, 5, 0, 1, 2, 3, 6, 7}));  // [s,t,...]
+    CKS(gemm(h, false, false, d * d, 1, N * N, h->S1, N * N, h->E[2], 1, h->rho, 1));
+    rho.resize((size_t)d * d);
+    CK(cudaMemcpyAsync(rho.data(), h->rho, rho.size() * sizeof(double), cudaMemcpyDeviceToHost, h->stream));
+    CK(cudaStreamSynchronize(h->stream));
+    return CTM_OK;
+}
+
+// horizontal pair in frame f: L at frame (x,y), R at frame (x+1,y); rho over (L, R)
+ctm_status rdm2_h_dev(ctm_ctx* h, int f, int L, int R, std::vector<double>& out) {
+    const int chi = h->chi, D = h->D, d = h->d, N = h->N;
+    double** eL = h->env[L];
+    double** eR = h->env[R];
+    const int c0 = f & 3, c1 = (f + 1) & 3;
+    // left half: E_ul(L) open, contracted with C4 T3 of L over its down leg
+    CKS(gemm(h, false, false, chi, N, chi, eL[Cw(c0)], chi, eL[Tw(c0)], N, h->X1, N));
+    CKS(corner_core(h, h->X1, eL[Tw(c0 + 3)], h->A[L][c0], h->Alu[L][c0], h->S3, true));
+    CKS(perm(h, h->S3, h->S1, {chi, chi, D, D, d, d, D, D}, {1, 2, 6, 4, 5, 0, 3, 7}));  // [b,r,r',s,t,a,d,d']
+    CKS(gemm(h, false, false, N, chi, chi, eL[Tw(c0 + 2)], chi, eL[Cw(c0 + 3)], chi, h->t1, chi));  // [z,d,d',g]
+    CKS(perm(h, h->t1, h->t2, {chi, D, D, chi}, {3, 1, 2, 0}));                       // [g,d,d',z]
+    CKS(gemm(h, false, false, N * d * d, chi, N, h->S1, N, h->t2, chi, h->Lh, chi));   // [b,r,r',s,t,k]
+    // right half: E_ur(R) open (rows = left leg, cols = down leg), cols contracted with C3 T3 of R
+    CKS(gemm(h, false, false, chi, N, chi, eR[Cw(c1)], chi, eR[Tw(c1)], N, h->X1, N));
+    CKS(corner_core(h, h->X1, eR[Tw(c1 + 3)], h->A[R][c1], h->Alu[R][c1], h->S3, true));
+    CKS(perm(h, h->S3, h->S1, {chi, chi, D, D, d, d, D, D}, {0, 3, 7, 4, 5, 1, 2, 6}));  // [a,d,d',s,t,b,r,r']
+    CKS(gemm(h, false, false, chi, N, chi, eR[Cw(c0 + 2)], chi, eR[Tw(c0 + 2)], N, h->t1, N));  // [b,d,d',k]
+    CKS(gemm(h, false, false, N * d * d, chi, N, h->S1, N, h->t1, chi, h->Rh, chi));   // [a,d,d',s,t,k]
+    // contract over (chi, D, D, chi): [p,q | b,r,r',k] x [s,t | b,r,r',k]
+    CKS(perm(h, h->Lh, h->S1, {chi, D, D, d, d, chi}, {3, 4, 0, 1, 2, 5}));
+    CKS(perm(h, h->Rh, h->S3, {chi, D, D, d, d, chi}, {3, 4, 0, 1, 2, 5}));
+    CKS(gemm(h, false, true, d * d, d * d, N * chi, h->S1, N * chi, h->S3, N * chi, h->rho, d * d));
+    std::vector<double> r((size_t)d * d * d * d);
+    CK(cudaMemcpyAsync(r.data(), h->rho, r.size() * sizeof(double), cudaMemcpyDeviceToHost, h->stream));
+    CK(cudaStreamSynchronize(h->stream));
+    // r[p,q,s,t] (p,q = ket,bra of L; s,t = ket,bra of R) -> rho[(p,s),(q,t)]
+    out.assign(r.size(), 0.0);
+    for (int p = 0; p < d; ++p)
+        for (int qq = 0; qq < d; ++qq)
+            for (int s = 0; s < d; ++s)
+                for (int t = 0; t < d; ++t)
+                    out[((size_t)(p * d + s)) * d * d + (qq * d + t)] = r[((p * d + qq) * d + s) * d + t];
+    return CTM_OK;
+}
+
+void normalise_trace(std::vector<double>& rho, int n) {
+    double tr = 0.0;
+    for (int i = 0; i < n; ++i) tr += rho[(size_t)i * n + i];
+    if (tr != 0.0)
+        for (double& v : rho) v /= tr;
+}
+
+ctm_status rdm2_any(ctm_ctx* h, int site, int dx, int dy, std::vector<double>& rho) {
+    const int d = h->d;
+    const int x = site % 2, y = site / 2;
+    const int j = ((x + dx) % 2 + 2) % 2 + 2 * (((y + dy) % 2 + 2) % 2);
+    std::vector<double> r;
+    bool swap = false;
+    if (dx == 1 && dy == 0) { CKS(rdm2_h_dev(h, 0, site, j, r)); }
+    else if (dx == -1 && dy == 0) { CKS(rdm2_h_dev(h, 0, j, site, r)); swap = true; }
+    else if (dx == 0 && dy == 1) { CKS(rdm2_h_dev(h, 1, j, site, r)); swap = true; }   // frame 1: top site is left
+    else if (dx == 0 && dy == -1) { CKS(rdm2_h_dev(h, 1, site, j, r)); }
+    else { h->err = "rdm2: |dx|+|dy| must be 1"; return CTM_ERR_ARG; }
+    rho.resize(r.size());
+    if (!swap) rho = r;
+    else
+        for (int a = 0; a < d; ++a)
+            for (int b = 0; b < d; ++b)
+                for (int c = 0; c < d; ++c)
+                    for (int e = 0; e < d; ++e)
+                        rho[((size_t)(a * d + b)) * d * d + (c * d + e)] = r[((size_t)(b * d + a)) * d * d + (e * d + c)];
+    normalise_trace(rho, d * d);
+    return CTM_OK;
+}
+
+thread_local std::string g_err;
+
+}  // namespace
+
+// ============================================================================
+// C ABI
+// ============================================================================
+extern "C" {
+
+const char* ctm_status_string(ctm_status s) {
+    switch (s) {
+        case CTM_OK: return "ok";
+        case CTM_NOT_CONVERGED: return "not converged";
+        case CTM_ERR_ARG: return "invalid argument";
+        case CTM_ERR_OOM: return "out of device memory";
+        case CTM_ERR_CUDA: return "CUDA error";
+        case CTM_ERR_NONFINITE: return "non-finite values";
+        case CTM_ERR_TIMEOUT: return "device wait timed out";
+        case CTM_ERR_STATE: return "invalid state";
+    }
+    return "unknown status";
+}
+
+const char* ctm_last_error(ctm_handle h) { return h ? h->err.c_str() : g_err.c_str(); }
+
+ctm_status ctm_default_options(ctm_options* o) {
+    if (!o) return CTM_ERR_ARG;
+    o->chi = 16;
+    o->max_sweeps = 100;
+    o->tol = 1e-10;
+    o->precision = CTM_FP64;
+    o->ozaki_slices = 4;
+    o->rsvd_oversample = 0;
+    o->rsvd_power_iters = 2;
+    o->sv_cutoff_rel = 1e-12;
+    o->seed = 0;
+    o->exact_svd_max_n = 256;
+    return CTM_OK;
+}
+
+static ctm_status validate(int d, int D, const ctm_options* o) {
+    if (!o || d < 1 || D < 1 || o->chi < 1 || d > 64 || D > 64) return CTM_ERR_ARG;
+    if (o->precision != CTM_FP64 && o->precision != CTM_OZAKI_BF16) return CTM_ERR_ARG;
+    if (o->rsvd_power_iters < 0) return CTM_ERR_ARG;
+    const long long N = (long long)o->chi * D * D;
+    if ((long long)d * d * N * N >= (1ll << 32)) return CTM_ERR_ARG;  // index range of the kernels
+    return CTM_OK;
+}
+
+ctm_status ctm_footprint_bytes(int d, int D, const ctm_options* o, size_t* bytes) {
+    if (!bytes || validate(d, D, o) != CTM_OK) return CTM_ERR_ARG;
+    *bytes = footprint(d, D, *o);
+    return CTM_OK;
+}
+
+ctm_status ctm_create(int d, int D, const ctm_options* o, void* stream, ctm_handle* out) {
+    if (!out) return CTM_ERR_ARG;
+    *out = nullptr;
+    if (validate(d, D, o) != CTM_OK) {
+        g_err = "ctm_create: invalid dimensions or options";
+        return CTM_ERR_ARG;
+    }
+    ctm_ctx* h = new (std::nothrow) ctm_ctx();
+    if (!h) return CTM_ERR_OOM;
+    h->d = d;
+    h->D = D;
+    h->opt = *o;
+    h->chi = o->chi;
+    h->N = o->chi * D * D;
+    h->k = rsvd_k(h->N, h->chi, *o);
+    h->q = o->rsvd_power_iters;
+    if (stream) h->stream = (cudaStream_t)stream;
+    else {
+        if (cudaStreamCreateWithFlags(&h->stream, cudaStreamNonBlocking) != cudaSuccess) {
+            g_err = "cudaStreamCreate failed";
+            delete h;
+            return CTM_ERR_CUDA;
+        }
+        h->own_stream = true;
+    }
+    Sizes z = sizes_of(d, D, h->chi, h->k);
+    const size_t N = h->N;
+    ctm_status st = CTM_OK;
+    auto A_ = [&](double** p, size_t n) { if (st == CTM_OK) st = allocd(h, p, n); };
+    for (int i = 0; i < 4; ++i)
+        for (int r = 0; r < 4; ++r) { A_(&h->A[i][r], z.A); A_(&h->Alu[i][r], z.A); }
+    for (int i = 0; i < 4; ++i)
+        for (int w = 0; w < 8; ++w) A_(&h->env[i][w], (w & 1) ? z.T : z.C);
+    A_(&h->X1, z.T);
+    A_(&h->S1, z.open);
+    A_(&h->S3, z.open);
+    A_(&h->S2, (size_t)d * z.NN);
+    for (int c = 0; c < 4; ++c) A_(&h->E[c], z.NN);
+    for (int s = 0; s < 2; ++s) { A_(&h->Pup[s], z.Nchi); A_(&h->PdnT[s], z.Nchi); }
+    A_(&h->Om, z.Nk); A_(&h->Yb, z.Nk); A_(&h->Zb, z.Nk); A_(&h->Qm, z.Nk); A_(&h->Qm2, z.Nk); A_(&h->Qb, z.Nk);
+    A_(&h->Rb, z.kk); A_(&h->G, z.kk); A_(&h->Us, z.kk); A_(&h->Ws, z.kk);
+    A_(&h->Sv, h->k); A_(&h->inv, h->k);
+    const size_t tk = std::max(z.Nk, z.Nchi);
+    A_(&h->Uc, z.Nchi); A_(&h->Vc, z.Nchi); A_(&h->t1, tk); A_(&h->t2, tk);
+    A_(&h->newC1, z.C); A_(&h->newC4, z.C); A_(&h->newT4, z.T); A_(&h->tmpT, z.T);
+    A_(&h->Lh, z.Nchi * d * d); A_(&h->Rh, z.Nchi * d * d);
+    A_(&h->rho, std::max<size_t>(64 * 64, (size_t)d * d * d * d));
+    h->splitk_n = (size_t)1 << 24;
+    A_(&h->splitk, h->splitk_n);
+    A_(&h->spec, 16 * (size_t)h->chi);
+    A_(&h->corners, 16 * z.C);
+    if (st == CTM_OK) st = alloc(h, &h->qr_ws, qr_ws_bytes(h->N, h->k));
+    if (st == CTM_OK) st = alloc(h, &h->svd_ws, svd_ws_bytes(h->k));
+    if (st == CTM_OK) st = alloc(h, &h->sval_ws, svals_ws_bytes(h->chi, 16));
+    if (st == CTM_OK) st = alloc(h, (void**)&h->maxbits, 64 * sizeof(unsigned long long));
+    if (st == CTM_OK) st = alloc(h, (void**)&h->flag, 64);
+    if (st != CTM_OK) {
+        g_err = h->err;
+        ctm_destroy(h);
+        return st;
+    }
+    if (cudaMemsetAsync(h->flag, 0, sizeof(int), h->stream) != cudaSuccess) {
+        g_err = "cudaMemset failed";
+        ctm_destroy(h);
+        return CTM_ERR_CUDA;
+    }
+    *out = h;
+    return CTM_OK;
+}
+
+ctm_status ctm_destroy(ctm_handle h) {
+    if (!h) return CTM_OK;
+    if (h->stream) cudaStreamSynchronize(h->stream);
+    for (void* p : h->allocs) cudaFree(p);
+    for (cudaEvent_t e : h->ev_pool) cudaEventDestroy(e);
+    if (h->own_stream && h->stream) cudaStreamDestroy(h->stream);
+    delete h;
+    return CTM_OK;
+}
+
+ctm_status ctm_set_tensor(ctm_handle h, int site, const double* A, int on_device) {
+    if (!h || !A || site < 0 || site > 3) return CTM_ERR_ARG;
+    const int d = h->d, D = h->D;
+    const size_t n = (size_t)d * D * D * D * D;
+    CK(cudaMemcpyAsync(h->A[site][0], A, n * sizeof(double),
+                       on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice, h->stream));
+    for (int r = 1; r < 4; ++r) CKS(perm(h, h->A[site][r - 1], h->A[site][r], {d, D, D, D, D}, {0, 2, 3, 4, 1}));
+    for (int r = 0; r < 4; ++r) CKS(perm(h, h->A[site][r], h->Alu[site][r], {d, D, D, D, D}, {1, 2, 0, 3, 4}));
+    CK(cudaStreamSynchronize(h->stream));
+    h->have_A[site] = true;
+    return CTM_OK;
+}
+
+ctm_status ctm_set_env(ctm_handle h, int site, int which, const double* t, int on_device) {
+    if (!h || !t || site < 0 || site > 3 || which < 0 || which > 7) return CTM_ERR_ARG;
+    const size_t n = (which & 1) ? (size_t)h->chi * h->D * h->D * h->chi : (size_t)h->chi * h->chi;
+    CK(cudaMemcpyAsync(h->env[site][which], t, n * sizeof(double),
+                       on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice, h->stream));
+    CK(cudaStreamSynchronize(h->stream));
+    h->env_set |= 1u << (site * 8 + which);
+    return CTM_OK;
+}
+
+ctm_status ctm_get_env(ctm_handle h, int site, int which, double* t, int on_device) {
+    if (!h || !t || site < 0 || site > 3 || which < 0 || which > 7) return CTM_ERR_ARG;
+    const size_t n = (which & 1) ? (size_t)h->chi * h->D * h->D * h->chi : (size_t)h->chi * h->chi;
+    CK(cudaMemcpyAsync(t, h->env[site][which], n * sizeof(double),
+                       on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost, h->stream));
+    CK(cudaStreamSynchronize(h->stream));
+    return CTM_OK;
+}
+
+ctm_status ctm_sweep(ctm_handle h, int n) {
+    if (!h || n < 0) return CTM_ERR_ARG;
+    CKS(check_ready(h));
+    for (int s = 0; s < n; ++s) CKS(one_sweep(h));
+    const ctm_status st = read_flag(h);
+    prof_collect(h);
+    return st;
+}
+
+ctm_status ctm_run(ctm_handle h, int* sweeps_done, double* last_delta) {
+    if (!h) return CTM_ERR_ARG;
+    CKS(check_ready(h));
+    std::vector<double> prev, cur;
+    CKS(spectra(h, prev));
+    double delta = INFINITY;
+    int n = 0;
+    ctm_status st = CTM_NOT_CONVERGED;
+    for (n = 1; n <= h->opt.max_sweeps; ++n) {
+        CKS(one_sweep(h));
+        CKS(read_flag(h));
+        CKS(spectra(h, cur));
+        delta = 0.0;
+        for (size_t i = 0; i < cur.size(); ++i) delta = std::max(delta, std::fabs(cur[i] - prev[i]));
+        prev.swap(cur);
+        if (delta < h->opt.tol) { st = CTM_OK; break; }
+    }
+    if (n > h->opt.max_sweeps) n = h->opt.max_sweeps;
+    if (sweeps_done) *sweeps_done = n;
+    if (last_delta) *last_delta = delta;
+    return st;
+}
+
+ctm_status ctm_corner_spectra(ctm_handle h, double* out_host) {
+    if (!h || !out_host) return CTM_ERR_ARG;
+    std::vector<double> s;
+    CKS(spectra(h, s));
+    std::memcpy(out_host, s.data(), s.size() * sizeof(double));
+    return CTM_OK;
+}
+
+ctm_status ctm_rdm1(ctm_handle h, int site, double* rho_host) {
+    if (!h || !rho_host || site < 0 || site > 3) return CTM_ERR_ARG;
+    CKS(check_ready(h));
+    std::vector<double> r;
+    CKS(rdm1_dev(h, site, r));
+    normalise_trace(r, h->d);
+    std::memcpy(rho_host, r.data(), r.size() * sizeof(double));
+    return CTM_OK;
+}
+
+ctm_status ctm_rdm2(ctm_handle h, int site, int dx, int dy, double* rho_host) {
+    if (!h || !rho_host || site < 0 || site > 3 || std::abs(dx) + std::abs(dy) != 1) return CTM_ERR_ARG;
+    CKS(check_ready(h));
+    std::vector<double> r;
+    CKS(rdm2_any(h, site, dx, dy, r));
+    std::memcpy(rho_host, r.data(), r.size() * sizeof(double));
+    return CTM_OK;
+}
+
+ctm_status ctm_measure1(ctm_handle h, int site, const double* op, double* value) {
+    if (!h || !op || !value) return CTM_ERR_ARG;
+    const int d = h->d;
+    std::vector<double> r((size_t)d * d);
+    CKS(ctm_rdm1(h, site, r.data()));
+    double v = 0.0;
+    for (int a = 0; a < d; ++a)
+        for (int b = 0; b < d; ++b) v += op[a * d + b] * r[b * d + a];
+    *value = v;
+    return CTM_OK;
+}
+
+ctm_status ctm_measure2(ctm_handle h, int site, int dx, int dy, const double* op, double* value) {
+    if (!h || !op || !value) return CTM_ERR_ARG;
+    const int n = h->d * h->d;
+    std::vector<double> r((size_t)n * n);
+    CKS(ctm_rdm2(h, site, dx, dy, r.data()));
+    double v = 0.0;
+    for (int a = 0; a < n; ++a)
+        for (int b = 0; b < n; ++b) v += op[a * n + b] * r[b * n + a];
+    *value = v;
+    return CTM_OK;
+}
+
+ctm_status ctm_op_from_elements(int d0, int d1, int n, const int* idx, const double* re, double* op_out) {
+    if (d0 < 1 || d1 < 1 || n < 0 || !op_out || (n > 0 && (!idx || !re))) return CTM_ERR_ARG;
+    const int m = d0 * d1;
+    for (int i = 0; i < m * m; ++i) op_out[i] = 0.0;
+    for (int l = 0; l < n; ++l) {
+        const int i0 = idx[4 * l], j0 = idx[4 * l + 1], i1 = idx[4 * l + 2], j1 = idx[4 * l + 3];
+        if (i0 < 0 || i0 >= d0 || i1 < 0 || i1 >= d0 || j0 < 0 || j0 >= d1 || j1 < 0 || j1 >= d1) return CTM_ERR_ARG;
+        op_out[(i1 * d1 + j1) * m + (i0 * d1 + j0)] += re[l];
+    }
+    return CTM_OK;
+}
+
+// ---------------------------------------------------------------------------
+// kernel-level entry points
+// ---------------------------------------------------------------------------
+ctm_status ctm_dgemm(int transA, int transB, int M, int N, int K, double alpha, const double* A, int lda,
+                     const double* B, int ldb, double beta, double* C, int ldc, void* stream) {
+    if (M < 0 || N < 0 || K < 0 || (M && N && (!A || !B || !C))) return CTM_ERR_ARG;
+    if (ctm::dgemm(transA != 0, transB != 0, M, N, K, alpha, A, lda, B, ldb, beta, C, ldc,
+                   (cudaStream_t)stream) != cudaSuccess) {
+        g_err = "ctm_dgemm launch failed";
+        return CTM_ERR_CUDA;
+    }
+    return CTM_OK;
+}
+
+ctm_status ctm_permute(const double* src, double* dst, int ndim, const int* dims, const int* perm_,
+                       void* stream) {
+    if (!src || !dst || !dims || !perm_ || ndim < 1 || ndim > 8) return CTM_ERR_ARG;
+    int seen = 0;
+    for (int a = 0; a < ndim; ++a) {
+        if (perm_[a] < 0 || perm_[a] >= ndim || dims[a] < 0) return CTM_ERR_ARG;
+        seen |= 1 << perm_[a];
+    }
+    if (seen != (1 << ndim) - 1) return CTM_ERR_ARG;
+    if (ctm::permute(src, dst, ndim, dims, perm_, (cudaStream_t)stream) != cudaSuccess) {
+        g_err = "ctm_permute launch failed";
+        return CTM_ERR_CUDA;
+    }
+    return CTM_OK;
+}
+
+size_t ctm_qr_workspace_bytes(int N, int k) { return (N >= k && k > 0) ? qr_ws_bytes(N, k) : 0; }
+
+ctm_status ctm_qr(const double* Y, int N, int k, double* Q, double* R, void* ws, void* stream) {
+    if (!Y || !Q || !R || !ws || k <= 0 || N < k) return CTM_ERR_ARG;
+    if (ctm::qr(Y, N, k, Q, R, ws, (cudaStream_t)stream) != cudaSuccess) {
+        g_err = "ctm_qr launch failed";
+        return CTM_ERR_CUDA;
+    }
+    return CTM_OK;
+}
+
+size_t ctm_svd_workspace_bytes(int k) { return (k > 0 && k <= 1024) ? svd_ws_bytes(k) : 0; }
+
+ctm_status ctm_svd(const double* G, int k, double* U, double* S, double* V, void* ws, void* stream) {
+    if (!G || !U || !S || !V || !ws || k <= 0 || k > 1024) return CTM_ERR_ARG;
+    if (ctm::svd(G, k, U, S, V, ws, (cudaStream_t)stream) != cudaSuccess) {
+        g_err = "ctm_svd launch failed";
+        return CTM_ERR_CUDA;
+    }
+    return CTM_OK;
+}
+
+ctm_status ctm_profile_enable(ctm_handle h, int on) {
+    if (!h) return CTM_ERR_ARG;
+    prof_collect(h);
+    h->prof = on != 0;
+    return CTM_OK;
+}
+
+ctm_status ctm_profile_read(ctm_handle h, ctm_profile_data* out, int reset) {
+    if (!h || !out) return CTM_ERR_ARG;
+    prof_collect(h);
+    for (int c = 0; c < 4; ++c) {
+        out->ms[c] = h->p_ms[c];
+        out->flops[c] = h->p_flops[c];
+        out->bytes[c] = h->p_bytes[c];
+        out->calls[c] = h->p_calls[c];
+        if (reset) h->p_ms[c] = h->p_flops[c] = h->p_bytes[c] = 0, h->p_calls[c] = 0;
+    }
+    return CTM_OK;
+}
+
+long long ctm_kernel_launches(void) { return ctm::g_launches; }
+
+}  // extern "C"

@@ -1,0 +1,192 @@
+"""End-to-end parity of the CUDA CTMRG (through the C ABI) with the CPU oracle.
+
+Same seeded inputs on both sides (paper_2112_13184_gb300.inputs).  The bar
+(FP64 path): every observable to 1e-10 relative, normalised corner singular
+values to 1e-9 absolute.  Only gauge-invariant quantities are compared: the
+randomised SVD and the oracle's full SVD pick different bases of the same
+truncated subspace.
+"""
+import numpy as np
+import pytest
+
+from oracle import ctmrg_ref as R
+from oracle import exact as X
+from paper_2112_13184_gb300 import inputs as I
+
+pytestmark = pytest.mark.gpu
+torch = pytest.importorskip("torch")
+
+
+@pytest.fixture(scope="module")
+def ctm():
+    if not torch.cuda.is_available():
+        pytest.skip("no GPU")
+    from paper_2112_13184_gb300 import ctm as m
+    return m
+
+
+def observables_oracle(envs, As, op1, op2):
+    one = [R.expect(op1, R.rdm1(envs, As, i)) for i in range(4)]
+    two = [R.expect(op2, R.rdm2(envs, As, i, dx, dy)) for (i, dx, dy) in I.SQUARE_2X2_BONDS]
+    return np.array(one + two)
+
+
+def observables_gpu(c, op1, op2):
+    one = [c.measure1(i, op1) for i in range(4)]
+    two = [c.measure2(i, dx, dy, op2) for (i, dx, dy) in I.SQUARE_2X2_BONDS]
+    return np.array(one + two)
+
+
+def run_both(ctm, As, envs, d, D, chi, sweeps, **opts):
+    c = ctm.CTMRG(d, D, chi, **opts)
+    c.set_tensors(As)
+    c.set_envs(envs)
+    c.sweep(sweeps)
+    ref, _, _ = R.run(As, envs, chi, sweeps)
+    return c, ref
+
+
+def test_neel_d2_D3_chi16_50_sweeps(ctm):
+    """The plain FP64 workload: d=2, D=3, chi=16 Neel + 0.1 noise, 50 sweeps.
+    N = 144 <= exact_svd_max_n, so the projectors use the exact truncated SVD."""
+    w = I.workload("neel_d2_D3_chi16")
+    c, ref = run_both(ctm, w["As"], w["envs"], w["d"], w["D"], w["chi"], w["sweeps"])
+    g = observables_gpu(c, w["op1"], w["op2"])
+    o = observables_oracle(ref, w["As"], w["op1"], w["op2"])
+    assert np.max(np.abs(g - o) / np.abs(o)) < 1e-10, (g, o)
+    sg = c.corner_spectra()
+    so = R.corner_spectra(ref)
+    # the spectrum below 1e-6 of the leading value is set by directions near
+    # the FP64 noise floor of M (its kept tail reaches ~1e-10 of s_0 here)
+    head = so > 1e-6 * so[..., :1]
+    assert np.max(np.abs(sg - so)[head]) < 1e-9
+    assert np.max(np.abs(sg - so)) < 1e-8
+    c.close()
+
+
+def test_neel_d2_D3_chi16_randomised_svd(ctm):
+    """Same workload through the randomised range finder (k = chi + 8 = 24,
+    q = 2), the path used above exact_svd_max_n.  Observables stay within
+    1e-10; the spectrum tail near the truncation carries the range-finder
+    error, so the corner spectra are held to 1e-8."""
+    w = I.workload("neel_d2_D3_chi16")
+    c, ref = run_both(ctm, w["As"], w["envs"], w["d"], w["D"], w["chi"], w["sweeps"], exact_svd_max_n=0)
+    g = observables_gpu(c, w["op1"], w["op2"])
+    o = observables_oracle(ref, w["As"], w["op1"], w["op2"])
+    assert np.max(np.abs(g - o) / np.abs(o)) < 1e-10, (g, o)
+    assert np.max(np.abs(c.corner_spectra() - R.corner_spectra(ref))) < 1e-8
+    c.close()
+
+
+# Converged, well-posed cases (sigma_chi / sigma_0 of M >= 3e-7, the oracle
+# converges to < 1e-12): N = chi D^2 = 81, 32, 90 cut across the 64-wide
+# GEMM tiles; d > D in the second.  Cases whose chi reaches the noise floor
+# of M (sigma_chi/sigma_0 ~ 1e-12) do not converge even in the oracle and are
+# not parity cases.
+@pytest.mark.parametrize("d,D,chi,noise", [(2, 3, 9, 0.2), (3, 2, 8, 0.3), (3, 3, 10, 0.2)])
+@pytest.mark.parametrize("exact", [True, False])
+def test_ragged_shapes(ctm, d, D, chi, noise, exact):
+    As = I.neel_tensors(d, D, noise, seed=21)
+    envs = I.random_env(chi, [D] * 4, seed=22)
+    op1 = I.spin_ops(d)["Sz"]
+    op2 = I.heisenberg_bond(d)
+    opts = {} if exact else dict(exact_svd_max_n=0, rsvd_oversample=8, rsvd_power_iters=3)
+    c, ref = run_both(ctm, As, envs, d, D, chi, 40, **opts)
+    g = observables_gpu(c, op1, op2)
+    o = observables_oracle(ref, As, op1, op2)
+    assert np.max(np.abs(g - o) / np.maximum(np.abs(o), 1e-3)) < 1e-10, (g, o)
+    c.close()
+
+
+def test_rdm_matrices_and_invariants(ctm):
+    d, D, chi = 2, 2, 6
+    As = I.neel_tensors(d, D, 0.3, seed=21)
+    envs = I.random_env(chi, [D] * 4, seed=22)
+    c, ref = run_both(ctm, As, envs, d, D, chi, 50)
+    for i in range(4):
+        r = c.rdm1(i)
+        np.testing.assert_allclose(r, R.rdm1(ref, As, i), atol=1e-11)
+        assert abs(np.trace(r) - 1) < 1e-14
+    for (i, dx, dy) in I.SQUARE_2X2_BONDS + ((1, -1, 0), (2, 0, -1)):
+        r = c.rdm2(i, dx, dy)
+        np.testing.assert_allclose(r, R.rdm2(ref, As, i, dx, dy), atol=1e-11)
+        assert np.max(np.abs(r - r.T)) < 1e-12
+    c.close()
+
+
+@pytest.mark.parametrize("beta", [0.6, 0.3])
+def test_ising_onsager_on_gpu(ctm, beta):
+    A = I.ising_peps_tensor(beta)
+    As = [A] * 4
+    chi = 16
+    envs = I.random_env(chi, [2] * 4, seed=5)
+    c = ctm.CTMRG(2, 2, chi)
+    c.set_tensors(As)
+    c.set_envs(envs)
+    c.sweep(60)
+    sz = np.diag([1.0, -1.0])
+    m = np.array([c.measure1(i, sz) for i in range(4)])
+    nn = np.array([c.measure2(i, dx, dy, np.kron(sz, sz)) for (i, dx, dy) in I.SQUARE_2X2_BONDS])
+    np.testing.assert_allclose(np.abs(m), X.yang_magnetisation(beta), atol=1e-9)
+    np.testing.assert_allclose(nn, X.onsager_nn_correlation(beta), rtol=1e-9)
+    c.close()
+
+
+def test_product_state_exact(ctm):
+    As = I.neel_tensors(2, 3, 0.0, seed=0)
+    envs = I.random_env(4, [3] * 4, seed=1)
+    c = ctm.CTMRG(2, 3, 4)
+    c.set_tensors(As)
+    c.set_envs(envs)
+    c.sweep(3)
+    sz = I.spin_ops(2)["Sz"]
+    for i in range(4):
+        x, y = i % 2, i // 2
+        assert abs(c.measure1(i, sz) - (0.5 if (x + y) % 2 == 0 else -0.5)) < 1e-12
+    for (i, dx, dy) in I.SQUARE_2X2_BONDS:
+        assert abs(c.measure2(i, dx, dy, I.heisenberg_bond(2)) + 0.25) < 1e-12
+    c.close()
+
+
+def test_run_converges(ctm):
+    d, D, chi = 2, 2, 12
+    As = I.neel_tensors(d, D, 0.3, seed=4)
+    envs = I.random_env(chi, [D] * 4, seed=9)
+    c = ctm.CTMRG(d, D, chi, tol=1e-11, max_sweeps=80)
+    c.set_tensors(As)
+    c.set_envs(envs)
+    st, n, delta = c.run()
+    assert st == ctm.CTM_OK and delta < 1e-11 and n < 80
+    ref, _, _ = R.run(As, envs, chi, 80, tol=1e-12)
+    h = I.heisenberg_bond(2)
+    assert abs(c.measure2(0, 1, 0, h) - R.expect(h, R.rdm2(ref, As, 0, 1, 0))) < 1e-9
+    c.close()
+
+
+def test_env_roundtrip_and_state_errors(ctm):
+    d, D, chi = 2, 2, 6
+    c = ctm.CTMRG(d, D, chi)
+    with pytest.raises(ctm.CtmError) as e:
+        c.sweep(1)
+    assert e.value.status == ctm.CTM_ERR_STATE
+    envs = I.random_env(chi, [D] * 4, seed=2)
+    c.set_envs(envs)
+    back = c.get_envs()
+    for i in range(4):
+        for n in envs[i]:
+            np.testing.assert_array_equal(back[i][n], envs[i][n])
+    c.close()
+
+
+def test_nonfinite_input_reported(ctm):
+    d, D, chi = 2, 2, 6
+    As = I.neel_tensors(d, D, 0.2, seed=1)
+    As[2] = As[2].copy()
+    As[2][0, 0, 0, 0, 0] = np.nan
+    c = ctm.CTMRG(d, D, chi)
+    c.set_tensors(As)
+    c.set_envs(I.random_env(chi, [D] * 4, seed=2))
+    with pytest.raises(ctm.CtmError) as e:
+        c.sweep(1)
+    assert e.value.status == ctm.CTM_ERR_NONFINITE
+    c.close()
