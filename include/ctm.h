@@ -188,6 +188,23 @@ size_t ctm_svd_workspace_bytes(int k);
 ctm_status ctm_svd(const double* G, int k, double* U, double* S, double* V, void* ws,
                    void* stream);
 
+/* ctm_svd without a caller workspace and without allocating (the paper has
+ * no counterpart; this is a deployment aid).  For callers that cannot call
+ * cudaMalloc where they need the SVD: cudaMalloc can synchronise the
+ * device, which is not allowed while a CUDA graph is being captured in
+ * global mode and stalls latency-bound serving loops, and callers that run
+ * under a fixed device-memory budget cannot make untracked allocations.
+ * The scratch (about 1 MB) lives in a static device array that every GPU
+ * loading libctm holds until the process exits; k must be <= 256, larger k
+ * returns CTM_ERR_ARG.  The first call on each device looks the array's
+ * device address up (with that device current); make that first call
+ * before any stream capture.  All calls share the one array, which keeps the
+ * previous call's contents (everything that must start at zero is cleared
+ * by the call itself): calls that can overlap on the GPU -- on different
+ * streams without ordering -- race and must be serialised by the caller.
+ * Arguments, layout and results are those of ctm_svd. */
+ctm_status ctm_svd_noalloc(const double* G, int k, double* U, double* S, double* V, void* stream);
+
 #ifdef __cplusplus
 }
 #endif

@@ -824,6 +824,21 @@ ctm_status ctm_svd(const double* G, int k, double* U, double* S, double* V, void
     return CTM_OK;
 }
 
+ctm_status ctm_svd_noalloc(const double* G, int k, double* U, double* S, double* V, void* stream) {
+    if (!G || !U || !S || !V) return CTM_ERR_ARG;
+    if (k <= 0 || k > ctm::svd_noalloc_max_k()) {
+        g_err = "ctm_svd_noalloc: k must be in 1.." + std::to_string(ctm::svd_noalloc_max_k()) +
+                " (size of the static scratch array)";
+        return CTM_ERR_ARG;
+    }
+    const cudaError_t e = ctm::svd_noalloc(G, k, U, S, V, (cudaStream_t)stream);
+    if (e != cudaSuccess) {
+        g_err = std::string("ctm_svd_noalloc: ") + cudaGetErrorString(e);
+        return CTM_ERR_CUDA;
+    }
+    return CTM_OK;
+}
+
 ctm_status ctm_profile_enable(ctm_handle h, int on) {
     if (!h) return CTM_ERR_ARG;
     prof_collect(h);

@@ -43,6 +43,9 @@ size_t qr_ws_bytes(int N, int k);
 cudaError_t qr(const double* Y, int N, int k, double* Q, double* R, void* ws, cudaStream_t s);
 size_t svd_ws_bytes(int k);
 cudaError_t svd(const double* G, int k, double* U, double* S, double* V, void* ws, cudaStream_t s);
+// svd() with its workspace in a static device array (k <= svd_noalloc_max_k())
+int svd_noalloc_max_k();
+cudaError_t svd_noalloc(const double* G, int k, double* U, double* S, double* V, cudaStream_t s);
 // singular values only (descending) of a batch of nb k x k matrices, each
 // normalised to sum 1; Gs contiguous, out nb*k
 size_t svals_ws_bytes(int k, int nb);

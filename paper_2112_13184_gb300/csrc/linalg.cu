@@ -6,6 +6,7 @@
 // waits on another.
 #include <cuda_runtime.h>
 #include <cstdint>
+#include <mutex>
 
 #include "internal.h"
 
@@ -348,6 +349,50 @@ cudaError_t svals_normalised(const double* Gs, int k, int nb, double* out, void*
     ++g_launches;
     k_svals_finish<<<nb, 256, sizeof(double) * k, s>>>(Gt, k, out);
     return cudaGetLastError();
+}
+
+// ---------------------------------------------------------------------------
+// Allocation-free SVD: the same Jacobi SVD with its scratch in a file-scope
+// device array.  The array's name in host code is only a host-side stand-in,
+// so the device address is looked up once per device with
+// cudaGetSymbolAddress (the first call on a device does this, with that
+// device current) and passed to the kernels like any other workspace.
+// ---------------------------------------------------------------------------
+namespace {
+constexpr int SVD_NOALLOC_MAX_K = 256;
+constexpr size_t SVD_NOALLOC_BYTES =
+    sizeof(double) * 2 * (size_t)SVD_NOALLOC_MAX_K * SVD_NOALLOC_MAX_K +
+    sizeof(unsigned long long) * JACOBI_MAX_SWEEPS + 256;
+static __device__ __align__(256) unsigned char g_svd_scratch[SVD_NOALLOC_BYTES];
+
+constexpr int MAX_DEVICES = 64;
+std::mutex g_scratch_mu;
+void* g_scratch_ptr[MAX_DEVICES] = {};
+}  // namespace
+
+int svd_noalloc_max_k() { return SVD_NOALLOC_MAX_K; }
+
+cudaError_t svd_noalloc(const double* G, int k, double* U, double* S, double* V, cudaStream_t s) {
+    if (k <= 0 || k > SVD_NOALLOC_MAX_K) return cudaErrorInvalidValue;
+    static_assert(SVD_NOALLOC_BYTES >= sizeof(double) * 2 * (size_t)SVD_NOALLOC_MAX_K * SVD_NOALLOC_MAX_K +
+                                           sizeof(unsigned long long) * JACOBI_MAX_SWEEPS,
+                  "scratch holds the Jacobi workspace of the largest k");
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return e;
+    if (dev < 0 || dev >= MAX_DEVICES) return cudaErrorInvalidDevice;
+    void* ws = nullptr;
+    {
+        std::lock_guard<std::mutex> lock(g_scratch_mu);
+        if (!g_scratch_ptr[dev]) {
+            void* p = nullptr;
+            e = cudaGetSymbolAddress(&p, g_svd_scratch);
+            if (e != cudaSuccess) return e;
+            g_scratch_ptr[dev] = p;
+        }
+        ws = g_scratch_ptr[dev];
+    }
+    return svd(G, k, U, S, V, ws, s);
 }
 
 }  // namespace ctm

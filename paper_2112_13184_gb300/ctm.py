@@ -78,6 +78,7 @@ _sig("ctm_qr", c_int, c_void_p, c_int, c_int, c_void_p, c_void_p, c_void_p, c_vo
 _sig("ctm_svd_workspace_bytes", c_size_t, c_int)
 _sig("ctm_svd", c_int, c_void_p, c_int, c_void_p, c_void_p, c_void_p, c_void_p, c_void_p)
 
+_sig("ctm_svd_noalloc", c_int, c_void_p, c_int, c_void_p, c_void_p, c_void_p, c_void_p)
 _sig("ctm_profile_enable", c_int, c_void_p, c_int)
 _sig("ctm_profile_read", c_int, c_void_p, ctypes.POINTER(ctm_profile_data), c_int)
 _sig("ctm_kernel_launches", ctypes.c_longlong)
@@ -272,6 +273,11 @@ def ctm_svd_workspace_bytes(k):
 def ctm_svd(G, k, U, S, V, ws, stream=None):
     _check(_lib.ctm_svd(_dev_ptr(G), k, _dev_ptr(U), _dev_ptr(S), _dev_ptr(V), ctypes.c_void_p(ws.data_ptr()),
                         _stream_ptr(stream)))
+
+
+def ctm_svd_noalloc(G, k, U, S, V, stream=None):
+    """ctm_svd with the library's static scratch (k <= 256); allocates nothing."""
+    _check(_lib.ctm_svd_noalloc(_dev_ptr(G), k, _dev_ptr(U), _dev_ptr(S), _dev_ptr(V), _stream_ptr(stream)))
 
 
 # ---------------------------------------------------------------------------
