@@ -78,7 +78,7 @@ typedef struct {
     int max_sweeps;         /* ctm_run: sweep cap                                 */
     double tol;             /* ctm_run: stop when the corner-spectrum change < tol */
     int precision;          /* ctm_precision                                       */
-    int ozaki_slices;       /* CTM_OZAKI_BF16: slices per operand, 3..6            */
+    int ozaki_slices;       /* CTM_OZAKI_BF16: slices per operand, 2..6            */
     int rsvd_oversample;    /* randomised SVD: k = min(chi + p, chi*D*D)           */
     int rsvd_power_iters;   /* randomised SVD: power iterations q                  */
     double sv_cutoff_rel;   /* S^{-1/2} := 0 for s < cutoff * s_0                  */
@@ -87,7 +87,7 @@ typedef struct {
                                everything and the truncated SVD is exact           */
 } ctm_options;
 
-/* Defaults: chi=16, max_sweeps=100, tol=1e-10, FP64, 4 slices,
+/* Defaults: chi=16, max_sweeps=100, tol=1e-10, FP64, 5 slices,
  * p=max(8,chi/8) (when rsvd_oversample<=0), q=2, cutoff 1e-12, seed 0,
  * exact_svd_max_n=256. */
 ctm_status ctm_default_options(ctm_options* opt);
@@ -187,6 +187,21 @@ ctm_status ctm_qr(const double* Y, int N, int k, double* Q, double* R, void* ws,
 size_t ctm_svd_workspace_bytes(int k);
 ctm_status ctm_svd(const double* G, int k, double* U, double* S, double* V, void* ws,
                    void* stream);
+
+/* C[M,N] = alpha op(A) op(B) + beta C like ctm_dgemm, computed on the tensor
+ * cores as exact BF16 slice products (emulated FP64; see CTM_OZAKI_BF16):
+ * each row of op(A) and column of op(B) is scaled by a power of two and cut
+ * into `slices` (2..6) signed 8-bit digits; products of the two leading
+ * digit levels are accumulated exactly, the rest in FP32, levels >= slices
+ * dropped.  Error ~ 2^(-8 slices) * max|row| * max|col| * K.  Entries whose
+ * digits all fit (e.g. integers below 2^8 per row max) give exact results.
+ * ws: ctm_gemm_ozaki_workspace_bytes(M,N,K,slices) bytes; its first int is
+ * set non-zero if a bounded wait inside the kernel gave up (C then holds no
+ * result).  Not synchronised. */
+size_t ctm_gemm_ozaki_workspace_bytes(int M, int N, int K, int slices);
+ctm_status ctm_gemm_ozaki(int transA, int transB, int M, int N, int K, double alpha, const double* A, int lda,
+                          const double* B, int ldb, double beta, double* C, int ldc, int slices, void* ws,
+                          void* stream);
 
 /* ctm_svd without a caller workspace and without allocating (the paper has
  * no counterpart; this is a deployment aid).  For callers that cannot call

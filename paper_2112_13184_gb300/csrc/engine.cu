@@ -18,6 +18,7 @@
 #include <cuda_runtime.h>
 
 #include <algorithm>
+#include <array>
 #include <cmath>
 #include <cstdio>
 #include <cstring>
@@ -83,6 +84,9 @@ struct ctm_ctx {
     double *Lh = nullptr, *Rh = nullptr, *rho = nullptr, *spec = nullptr, *corners = nullptr;
     double* splitk = nullptr;  // split-K partial sums
     size_t splitk_n = 0;
+    // emulated-FP64 tensor-core GEMMs: operand slices and split-K partials
+    void *ozA = nullptr, *ozB = nullptr, *ozW = nullptr;
+    size_t ozA_n = 0, ozB_n = 0, ozW_n = 0;
     // optional per-class device timing (ctm_profile_*)
     bool prof = false;
     std::vector<cudaEvent_t> ev_pool;
@@ -138,6 +142,28 @@ int rsvd_k(int N, int chi, const ctm_options& o) {
     return std::min(N, chi + p);
 }
 
+// every (M, N, K) a sweep or an RDM contracts (GEMM calls of this file)
+std::vector<std::array<long long, 3>> gemm_shapes(int d, int D, int chi, int k) {
+    const long long N = (long long)chi * D * D, D2 = (long long)D * D, M3 = (long long)chi * chi * D2;
+    return {{chi, N, chi},      {N, N, chi},          {M3, d * D2, D2},     {M3, D2, d * D2},
+            {M3 * d, d * D2, D2}, {N, k, N},          {N, chi, k},          {N, chi, N},
+            {chi, chi, N},      {chi, N, N},          {N, chi, chi},        {N * D2, chi, chi},
+            {(long long)d * d, 1, N * N}, {N * d * d, chi, N}, {(long long)d * d, (long long)d * d, N * chi}};
+}
+
+struct OzBounds {
+    size_t a = 0, b = 0, w = 0;
+};
+OzBounds oz_bounds(int d, int D, int chi, int k, int s) {
+    OzBounds z;
+    for (const auto& sh : gemm_shapes(d, D, chi, k)) {
+        z.a = std::max(z.a, ctm::oz_split_bytes((int)sh[0], (int)sh[2], s));
+        z.b = std::max(z.b, ctm::oz_split_bytes((int)sh[1], (int)sh[2], s));
+        z.w = std::max(z.w, ctm::oz_gemm_ws_bytes((int)sh[0], (int)sh[1], (int)sh[2], s));
+    }
+    return z;
+}
+
 size_t footprint(int d, int D, const ctm_options& o) {
     const int chi = o.chi;
     const int N = chi * D * D;
@@ -160,6 +186,10 @@ size_t footprint(int d, int D, const ctm_options& o) {
     size_t bytes = dbl * sizeof(double);
     bytes += qr_ws_bytes(N, k) + svd_ws_bytes(k) + svals_ws_bytes(chi, 16);
     bytes += 64 * sizeof(unsigned long long) + 64 + 64 * 256;
+    if (o.precision == CTM_OZAKI_BF16) {
+        const OzBounds z = oz_bounds(d, D, chi, k, o.ozaki_slices);
+        bytes += z.a + z.b + z.w + 3 * 256;
+    }
     return bytes;
 }
 
@@ -222,7 +252,21 @@ void prof_collect(ctm_ctx* h) {
 ctm_status gemm(ctm_ctx* h, bool tA, bool tB, int M, int N, int K, const double* A, int lda,
                 const double* B, int ldb, double* C, int ldc, double beta = 0.0) {
     const size_t ev = prof_begin(h);
-    CK(ctm::dgemm(tA, tB, M, N, K, 1.0, A, lda, B, ldb, beta, C, ldc, h->stream, h->splitk, h->splitk_n));
+    // a matrix-vector product gains nothing from 128-wide tensor tiles
+    if (h->opt.precision == CTM_OZAKI_BF16 && M > 0 && N > 1 && K > 0) {
+        const int s = h->opt.ozaki_slices;
+        if (ctm::oz_split_bytes(M, K, s) > h->ozA_n || ctm::oz_split_bytes(N, K, s) > h->ozB_n ||
+            ctm::oz_gemm_ws_bytes(M, N, K, s) > h->ozW_n) {
+            h->err = "emulated GEMM: shape outside the handle's workspace";
+            return CTM_ERR_STATE;
+        }
+        // op(A)[m][k] and op(B)[k][n] as row views of M x K and N x K
+        CK(ctm::oz_split(A, M, K, tA ? 1 : lda, tA ? lda : 1, s, h->ozA, h->stream));
+        CK(ctm::oz_split(B, N, K, tB ? ldb : 1, tB ? 1 : ldb, s, h->ozB, h->stream));
+        CK(ctm::oz_gemm(M, N, K, s, h->ozA, h->ozB, 1.0, beta, C, ldc, h->ozW, h->ozW_n, h->flag + 1, h->stream));
+    } else {
+        CK(ctm::dgemm(tA, tB, M, N, K, 1.0, A, lda, B, ldb, beta, C, ldc, h->stream, h->splitk, h->splitk_n));
+    }
     prof_end(h, ev, P_GEMM, 2.0 * M * N * K, 8.0 * ((double)M * K + (double)K * N + (double)M * N));
     return CTM_OK;
 }
@@ -398,10 +442,14 @@ ctm_status check_ready(ctm_ctx* h) {
 }
 
 ctm_status read_flag(ctm_ctx* h) {
-    int f = 0;
-    CK(cudaMemcpyAsync(&f, h->flag, sizeof(int), cudaMemcpyDeviceToHost, h->stream));
+    int f[2] = {0, 0};
+    CK(cudaMemcpyAsync(f, h->flag, 2 * sizeof(int), cudaMemcpyDeviceToHost, h->stream));
     CK(cudaStreamSynchronize(h->stream));
-    if (f) {
+    if (f[1]) {
+        h->err = "a bounded wait inside a tensor-core GEMM gave up";
+        return CTM_ERR_TIMEOUT;
+    }
+    if (f[0]) {
         h->err = "non-finite environment";
         return CTM_ERR_NONFINITE;
     }
@@ -541,7 +589,7 @@ ctm_status ctm_default_options(ctm_options* o) {
     o->max_sweeps = 100;
     o->tol = 1e-10;
     o->precision = CTM_FP64;
-    o->ozaki_slices = 4;
+    o->ozaki_slices = 5;
     o->rsvd_oversample = 0;
     o->rsvd_power_iters = 2;
     o->sv_cutoff_rel = 1e-12;
@@ -554,6 +602,7 @@ static ctm_status validate(int d, int D, const ctm_options* o) {
     if (!o || d < 1 || D < 1 || o->chi < 1 || d > 64 || D > 64) return CTM_ERR_ARG;
     if (o->precision != CTM_FP64 && o->precision != CTM_OZAKI_BF16) return CTM_ERR_ARG;
     if (o->rsvd_power_iters < 0) return CTM_ERR_ARG;
+    if (o->precision == CTM_OZAKI_BF16 && (o->ozaki_slices < 2 || o->ozaki_slices > 6)) return CTM_ERR_ARG;
     const long long N = (long long)o->chi * D * D;
     if ((long long)d * d * N * N >= (1ll << 32)) return CTM_ERR_ARG;  // index range of the kernels
     return CTM_OK;
@@ -621,12 +670,21 @@ ctm_status ctm_create(int d, int D, const ctm_options* o, void* stream, ctm_hand
     if (st == CTM_OK) st = alloc(h, &h->sval_ws, svals_ws_bytes(h->chi, 16));
     if (st == CTM_OK) st = alloc(h, (void**)&h->maxbits, 64 * sizeof(unsigned long long));
     if (st == CTM_OK) st = alloc(h, (void**)&h->flag, 64);
+    if (st == CTM_OK && o->precision == CTM_OZAKI_BF16) {
+        const OzBounds zb = oz_bounds(d, D, h->chi, h->k, o->ozaki_slices);
+        h->ozA_n = zb.a;
+        h->ozB_n = zb.b;
+        h->ozW_n = std::max<size_t>(zb.w, 256);
+        st = alloc(h, &h->ozA, h->ozA_n);
+        if (st == CTM_OK) st = alloc(h, &h->ozB, h->ozB_n);
+        if (st == CTM_OK) st = alloc(h, &h->ozW, h->ozW_n);
+    }
     if (st != CTM_OK) {
         g_err = h->err;
         ctm_destroy(h);
         return st;
     }
-    if (cudaMemsetAsync(h->flag, 0, sizeof(int), h->stream) != cudaSuccess) {
+    if (cudaMemsetAsync(h->flag, 0, 64, h->stream) != cudaSuccess) {
         g_err = "cudaMemset failed";
         ctm_destroy(h);
         return CTM_ERR_CUDA;
@@ -834,6 +892,37 @@ ctm_status ctm_svd_noalloc(const double* G, int k, double* U, double* S, double*
     const cudaError_t e = ctm::svd_noalloc(G, k, U, S, V, (cudaStream_t)stream);
     if (e != cudaSuccess) {
         g_err = std::string("ctm_svd_noalloc: ") + cudaGetErrorString(e);
+        return CTM_ERR_CUDA;
+    }
+    return CTM_OK;
+}
+
+size_t ctm_gemm_ozaki_workspace_bytes(int M, int N, int K, int slices) {
+    if (M <= 0 || N <= 0 || K <= 0 || slices < 2 || slices > 6) return 0;
+    return 256 + ctm::oz_split_bytes(M, K, slices) + ctm::oz_split_bytes(N, K, slices) +
+           ctm::oz_gemm_ws_bytes(M, N, K, slices);
+}
+
+ctm_status ctm_gemm_ozaki(int transA, int transB, int M, int N, int K, double alpha, const double* A, int lda,
+                          const double* B, int ldb, double beta, double* C, int ldc, int slices, void* ws,
+                          void* stream) {
+    if (M < 0 || N < 0 || K <= 0 || slices < 2 || slices > 6 || (M && N && (!A || !B || !C || !ws)))
+        return CTM_ERR_ARG;
+    if (!M || !N) return CTM_OK;
+    cudaStream_t st = (cudaStream_t)stream;
+    char* w = (char*)ws;
+    int* err = (int*)w;
+    void* sa = w + 256;
+    void* sb = (char*)sa + ctm::oz_split_bytes(M, K, slices);
+    void* part = (char*)sb + ctm::oz_split_bytes(N, K, slices);
+    cudaError_t e = cudaMemsetAsync(err, 0, sizeof(int), st);
+    if (e == cudaSuccess) e = ctm::oz_split(A, M, K, transA ? 1 : lda, transA ? lda : 1, slices, sa, st);
+    if (e == cudaSuccess) e = ctm::oz_split(B, N, K, transB ? ldb : 1, transB ? 1 : ldb, slices, sb, st);
+    if (e == cudaSuccess)
+        e = ctm::oz_gemm(M, N, K, slices, sa, sb, alpha, beta, C, ldc, part,
+                         ctm::oz_gemm_ws_bytes(M, N, K, slices), err, st);
+    if (e != cudaSuccess) {
+        g_err = std::string("ctm_gemm_ozaki: ") + cudaGetErrorString(e);
         return CTM_ERR_CUDA;
     }
     return CTM_OK;

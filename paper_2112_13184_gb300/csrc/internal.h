@@ -51,4 +51,14 @@ cudaError_t svd_noalloc(const double* G, int k, double* U, double* S, double* V,
 size_t svals_ws_bytes(int k, int nb);
 cudaError_t svals_normalised(const double* Gs, int k, int nb, double* out, void* ws, cudaStream_t s);
 
+// ---- emulated-FP64 GEMM on the tensor cores (ozaki.cu) ----------------------
+// Split an R x K FP64 operand (element (r,k) at X[r*rs + k*cs]) into s BF16
+// slices [s][R][K8] plus per-row exponents, in a buffer of oz_split_bytes.
+size_t oz_split_bytes(int R, int K, int s);
+cudaError_t oz_split(const double* X, int R, int K, long long rs, long long cs, int s, void* buf, cudaStream_t st);
+// C[M,N] = alpha A B + beta C from split A (M rows) and split B (N rows = columns of B).
+size_t oz_gemm_ws_bytes(int M, int N, int K, int s);
+cudaError_t oz_gemm(int M, int N, int K, int s, const void* Asplit, const void* Bsplit, double alpha, double beta,
+                    double* C, int ldc, void* ws, size_t ws_bytes, int* err, cudaStream_t st);
+
 }  // namespace ctm

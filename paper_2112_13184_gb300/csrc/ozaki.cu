@@ -1,0 +1,655 @@
+// Emulated-FP64 GEMM on the GB300 tensor cores (tcgen05 + TMEM + TMA).
+//
+// Each FP64 operand row (of A) or column (of B) is scaled by a power of two
+// 2^e with max|x| <= 2^e and cut into s signed 8-bit digits,
+//     x = 2^(e-8) * sum_t a_t 2^(-8t),   a_0 in [-256,256], a_t in [-128,127],
+// computed with integer operations on the FP64 bit pattern (the FP64 pipe of
+// GB300 is slow).  The scaled digits at_t = a_t 2^(-8t) are exact in BF16.
+// C = A B is then the sum of BF16 slice products at_t * bt_u:
+//   level 0 (t+u = 0) and level 1 (t+u = 1) are integer-valued (in units of
+//   1 and 2^-8); summed in FP32 over K-chunks of 256 they stay below 2^24
+//   units and are therefore exact; every chunk is read out of TMEM and
+//   added to int32 registers;
+//   all pairs with 2 <= t+u <= s-1 carry a weight <= 2^-16 and go into one
+//   FP32 accumulator whose rounding is below the slicing error;
+//   pairs with t+u >= s are dropped (same order as the slicing error).
+// The result is assembled in FP64:  C = 2^(eA+eB-16) (S0 + 2^-8 S1 + F).
+// Accuracy ~ 2^(-8s) of max|row| * max|col| * K, against FP32-accumulated
+// split-BF16 which cannot go below ~2^-24.
+#include <cuda.h>
+#include <cuda_bf16.h>
+#include <cuda_runtime.h>
+#include <cudaTypedefs.h>
+
+#include <algorithm>
+#include <cstdint>
+#include <mutex>
+
+#include "internal.h"
+
+namespace ctm {
+namespace oz {
+
+constexpr int BM = 128;          // rows per CTA (one TMEM lane per row)
+constexpr int BK = 32;           // K per pipeline stage (64 bytes: one SW64 row)
+constexpr int CHUNK_KB = 8;      // k-blocks per exact chunk (K = 256)
+constexpr int EPI_WARPS = 12;    // 3 warps per TMEM lane quarter
+constexpr int THREADS = (EPI_WARPS + 2) * 32;  // + producer warp + MMA warp
+constexpr int MAX_S = 6;
+
+// ---------------------------------------------------------------------------
+// slicing
+// ---------------------------------------------------------------------------
+// exponent e with max|x| < 2^e (0 for an all-zero row)
+__device__ __forceinline__ int row_exponent(double mx) {
+    if (mx == 0.0) return 0;
+    const int E = (int)((__double_as_longlong(mx) >> 52) & 0x7ff);
+    return E == 0 ? -1022 : E - 1022;
+}
+
+// signed base-256 digits of round(x * 2^(8s - e)); |x| <= 2^e
+__device__ __forceinline__ void digits(double x, int e, int s, int* d) {
+    const unsigned long long b = (unsigned long long)__double_as_longlong(x);
+    int ex = (int)((b >> 52) & 0x7ff);
+    unsigned long long mant = b & ((1ull << 52) - 1);
+    if (ex == 0) ex = 1;
+    else mant |= 1ull << 52;
+    const int shift = ex - 1075 + 8 * s - e;  // x = mant 2^(ex-1075)
+    long long Y;
+    if (mant == 0) Y = 0;
+    else if (shift >= 0) Y = (long long)(mant << shift);  // <= 2^(8s) by |x| <= 2^e
+    else {
+        const int sh = -shift;
+        Y = sh >= 54 ? 0 : (long long)((mant + (1ull << (sh - 1))) >> sh);
+    }
+    if (b >> 63) Y = -Y;
+#pragma unroll
+    for (int t = MAX_S - 1; t >= 1; --t) {
+        if (t < s) {
+            const long long dd = ((Y + 128) & 255) - 128;
+            d[t] = (int)dd;
+            Y = (Y - dd) >> 8;
+        }
+    }
+    d[0] = (int)Y;
+}
+
+__device__ __forceinline__ __nv_bfloat16 slice_value(int digit, int t) {
+    // digit * 2^(-8t): at most 9 significant bits, exact in FP32 and BF16
+    return __float2bfloat16_rn(ldexpf((float)digit, -8 * t));
+}
+
+// K contiguous (cs == 1): one warp per row.
+__global__ void k_split_rows(const double* __restrict__ X, int R, int K, int K8, long long rs, int s,
+                             __nv_bfloat16* __restrict__ out, int* __restrict__ ex) {
+    const int warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5, lane = threadIdx.x & 31;
+    if (warp >= R) return;
+    const double* x = X + (size_t)warp * rs;
+    double mx = 0.0;
+    for (int k = lane; k < K; k += 32) mx = fmax(mx, fabs(x[k]));
+    for (int o = 16; o > 0; o >>= 1) mx = fmax(mx, __shfl_xor_sync(0xffffffffu, mx, o));
+    const int e = row_exponent(mx);
+    if (lane == 0) ex[warp] = e;
+    const size_t plane = (size_t)R * K8;
+    __nv_bfloat16* o = out + (size_t)warp * K8;
+    for (int k = lane; k < K8; k += 32) {
+        int d[MAX_S];
+        if (k < K) digits(x[k], e, s, d);
+        else
+            for (int t = 0; t < MAX_S; ++t) d[t] = 0;
+        for (int t = 0; t < s; ++t) o[t * plane + k] = slice_value(d[t], t);
+    }
+}
+
+// General strides (rows contiguous when rs == 1).  Pass 1: per-row max|x|
+// over K, the grid split over (32-row groups, K ranges), combined with
+// atomicMax on the bit pattern.  Pass 2: a warp takes 32 rows x 32 k (lane =
+// row while reading, so reads along contiguous rows coalesce), staged
+// through shared memory so that the K-major slice writes coalesce too.
+constexpr int COLS_KRANGE = 256;
+
+__global__ void k_rowmax_cols(const double* __restrict__ X, int R, int K, long long rs, long long cs,
+                              unsigned long long* __restrict__ maxbits) {
+    const int r = blockIdx.x * 32 + (threadIdx.x & 31);
+    const int k0 = (blockIdx.y * (blockDim.x >> 5) + (threadIdx.x >> 5)) * COLS_KRANGE;
+    if (r >= R || k0 >= K) return;
+    const int k1 = min(K, k0 + COLS_KRANGE);
+    double mx = 0.0;
+    for (int k = k0; k < k1; ++k) mx = fmax(mx, fabs(X[(size_t)r * rs + (size_t)k * cs]));
+    atomicMax(maxbits + r, (unsigned long long)__double_as_longlong(mx));
+}
+
+__global__ void k_split_cols(const double* __restrict__ X, int R, int K, int K8, long long rs, long long cs,
+                             int s, const unsigned long long* __restrict__ maxbits, __nv_bfloat16* __restrict__ out,
+                             int* __restrict__ ex) {
+    __shared__ __nv_bfloat16 tile[2][MAX_S][32][33];  // launched with 2 warps
+    const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int r0 = blockIdx.x * 32;
+    const int k0 = (blockIdx.y * 2 + w) * 32;
+    if (k0 >= K8) return;
+    const int r = r0 + lane;
+    const bool live = r < R;
+    const int e = live ? row_exponent(__longlong_as_double((long long)maxbits[r])) : 0;
+    if (live && k0 == 0) ex[r] = e;
+    for (int kk = 0; kk < 32; ++kk) {
+        const int k = k0 + kk;
+        int d[MAX_S];
+        if (live && k < K) digits(X[(size_t)r * rs + (size_t)k * cs], e, s, d);
+        else
+            for (int t = 0; t < MAX_S; ++t) d[t] = 0;
+        for (int t = 0; t < s; ++t) tile[w][t][lane][kk] = slice_value(d[t], t);
+    }
+    __syncwarp();
+    const size_t plane = (size_t)R * K8;
+    const int k = k0 + lane;
+    if (k < K8)
+        for (int rr = 0; rr < 32 && r0 + rr < R; ++rr)
+            for (int t = 0; t < s; ++t) out[t * plane + (size_t)(r0 + rr) * K8 + k] = tile[w][t][rr][lane];
+}
+
+// ---------------------------------------------------------------------------
+// PTX helpers: mbarrier, TMA, tcgen05
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ uint32_t smem_u32(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
+
+__device__ __forceinline__ void mbar_init(uint64_t* bar, uint32_t count) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count) : "memory");
+}
+__device__ __forceinline__ void mbar_expect_tx(uint64_t* bar, uint32_t bytes) {
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)), "r"(bytes)
+                 : "memory");
+}
+__device__ __forceinline__ void mbar_arrive(uint64_t* bar) {
+    asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(bar)) : "memory");
+}
+__device__ __forceinline__ bool mbar_try_wait(uint64_t* bar, uint32_t parity) {
+    uint32_t ok;
+    asm volatile(
+        "{\n\t.reg .pred p;\n\t"
+        "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+        "selp.u32 %0, 1, 0, p;\n\t}"
+        : "=r"(ok)
+        : "r"(smem_u32(bar)), "r"(parity)
+        : "memory");
+    return ok != 0;
+}
+// Bounded wait: gives up after ~2e9 cycles, or at once when another thread
+// has already given up, recording the failure in *err.
+__device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity, int* err) {
+    const long long t0 = clock64();
+    while (!mbar_try_wait(bar, parity)) {
+        if (*(volatile int*)err) return false;
+        if (clock64() - t0 > 2000000000ll) {
+            atomicCAS(err, 0, 1);
+            return false;
+        }
+    }
+    return true;
+}
+
+__device__ __forceinline__ void tma_load_3d(void* dst, const CUtensorMap* map, int c0, int c1, int c2,
+                                            uint64_t* bar) {
+    asm volatile(
+        "cp.async.bulk.tensor.3d.shared::cluster.global.tile.mbarrier::complete_tx::bytes"
+        " [%0], [%1, {%2, %3, %4}], [%5];" ::"r"(smem_u32(dst)),
+        "l"((uint64_t)map), "r"(c0), "r"(c1), "r"(c2), "r"(smem_u32(bar))
+        : "memory");
+}
+
+__device__ __forceinline__ void tc_fence_before() { asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory"); }
+__device__ __forceinline__ void tc_fence_after() { asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory"); }
+
+__device__ __forceinline__ void tc_mma(uint32_t d_tmem, uint64_t a_desc, uint64_t b_desc, uint32_t idesc,
+                                       uint32_t accumulate) {
+    asm volatile(
+        "{\n\t.reg .pred p;\n\t"
+        "setp.ne.b32 p, %4, 0;\n\t"
+        "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}" ::"r"(d_tmem),
+        "l"(a_desc), "l"(b_desc), "r"(idesc), "r"(accumulate)
+        : "memory");
+}
+__device__ __forceinline__ void tc_commit(uint64_t* bar) {
+    asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
+                     smem_u32(bar))
+                 : "memory");
+}
+__device__ __forceinline__ void tc_ld16(uint32_t taddr, uint32_t* r) {
+    asm volatile(
+        "tcgen05.ld.sync.aligned.32x32b.x16.b32 "
+        "{%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, [%16];"
+        : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
+          "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15])
+        : "r"(taddr));
+}
+__device__ __forceinline__ void tc_wait_ld() { asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory"); }
+
+// Shared-memory matrix descriptor of a K-major, 64-byte-swizzled tile
+// (rows of 64 bytes, 8-row groups 512 bytes apart).
+__device__ __forceinline__ uint64_t sw64_desc(uint32_t saddr) {
+    uint64_t d = 0;
+    d |= (uint64_t)((saddr >> 4) & 0x3FFF);
+    d |= (uint64_t)1 << 16;                 // leading byte offset (unused for swizzled K-major)
+    d |= (uint64_t)(512 >> 4) << 32;        // stride byte offset: 8 rows x 64 B
+    d |= (uint64_t)1 << 46;                 // descriptor version
+    d |= (uint64_t)4 << 61;                 // SWIZZLE_64B
+    return d;
+}
+
+
+// ---------------------------------------------------------------------------
+// slice GEMM
+// ---------------------------------------------------------------------------
+struct GemmArgs {
+    int M, N;             // logical output size
+    int nkb;              // 32-wide k-blocks in K
+    int kb_per_split;     // k-blocks per blockIdx.z (a multiple of CHUNK_KB)
+    int s;                // slices per operand
+    int stages;
+    uint32_t a_bytes, stage_bytes;
+    const int* eA;        // row exponents of A (M)
+    const int* eB;        // column exponents of B (N)
+    int direct;           // 1: write C; 0: write split-K partials
+    double alpha, beta;
+    double* C;
+    int ldc;
+    int* PS0;             // partials [z][Mpad][Npad]
+    int* PS1;
+    float* PF;
+    int Mpad, Npad;
+    int* err;
+};
+
+template <int NB16>
+__global__ void __launch_bounds__(THREADS, 1)
+    k_oz_gemm(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB, const GemmArgs g) {
+    constexpr int BN = 16 * NB16;
+    constexpr int NBG = (NB16 + 2) / 3;  // 16-column blocks per epilogue warp
+    constexpr uint32_t TMEM_COLS = (3 * BN <= 32) ? 32 : (3 * BN <= 64) ? 64 : (3 * BN <= 128) ? 128
+                                   : (3 * BN <= 256) ? 256 : 512;
+    extern __shared__ uint8_t smem_raw[];
+    const uint32_t raw = smem_u32(smem_raw);
+    const uint32_t base = (raw + 1023u) & ~1023u;
+    uint8_t* sbase = smem_raw + (base - raw);
+    uint64_t* full = (uint64_t*)(sbase + (size_t)g.stages * g.stage_bytes);
+    uint64_t* empty = full + g.stages;
+    uint64_t* acc_full = empty + g.stages;
+    uint64_t* acc_empty = acc_full + 1;
+    uint64_t* drain = acc_full + 2;
+    uint32_t* tmem_slot = (uint32_t*)(drain + 1);
+
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int m0 = blockIdx.x * BM, n0 = blockIdx.y * BN;
+    const int kb0 = blockIdx.z * g.kb_per_split;
+    const int kb1 = min(g.nkb, kb0 + g.kb_per_split);
+    const int nkb = kb1 - kb0;
+    const int nchunks = (nkb + CHUNK_KB - 1) / CHUNK_KB;
+
+    if (warp == 0) {
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(tmem_slot)),
+                     "r"(TMEM_COLS)
+                     : "memory");
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+    }
+    if (threadIdx.x == 32) {
+        for (int st = 0; st < g.stages; ++st) {
+            mbar_init(&full[st], 1);
+            mbar_init(&empty[st], 1);
+        }
+        mbar_init(acc_full, 1);
+        mbar_init(acc_empty, EPI_WARPS);
+        mbar_init(drain, 1);
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    tc_fence_before();
+    __syncthreads();
+    tc_fence_after();
+    const uint32_t tmem = *tmem_slot;
+
+    if (warp == EPI_WARPS) {
+        // ---------------- TMA producer ----------------
+        if (lane == 0) {
+            int issued = 0;
+            for (int i = 0; i < nkb; ++i) {
+                const int st = i % g.stages;
+                const uint32_t ph = (uint32_t)(i / g.stages) & 1u;
+                if (!mbar_wait(&empty[st], ph ^ 1u, g.err)) break;
+                uint8_t* sa = sbase + (size_t)st * g.stage_bytes;
+                mbar_expect_tx(&full[st], g.stage_bytes);
+                const int kc = (kb0 + i) * BK;
+                tma_load_3d(sa, &tmA, kc, m0, 0, &full[st]);
+                tma_load_3d(sa + g.a_bytes, &tmB, kc, n0, 0, &full[st]);
+                ++issued;
+            }
+            if (*(volatile int*)g.err) {
+                // let the copies still in flight land before the CTA exits
+                for (int i = max(0, issued - g.stages); i < issued; ++i) {
+                    const long long t0 = clock64();
+                    while (!mbar_try_wait(&full[i % g.stages], (uint32_t)(i / g.stages) & 1u) &&
+                           clock64() - t0 < 2000000000ll) {
+                    }
+                }
+            }
+        }
+    } else if (warp == EPI_WARPS + 1) {
+        // ---------------- MMA issuer ----------------
+        if (lane == 0) {
+            const uint32_t idesc = (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(BN >> 3) << 17) |
+                                   ((uint32_t)(BM >> 4) << 24);
+            for (int i = 0; i < nkb; ++i) {
+                const int st = i % g.stages;
+                const uint32_t ph = (uint32_t)(i / g.stages) & 1u;
+                const int chunk = i / CHUNK_KB;
+                const bool first = (i % CHUNK_KB) == 0;
+                const bool last = (i % CHUNK_KB) == CHUNK_KB - 1 || i == nkb - 1;
+                if (first && chunk > 0 && !mbar_wait(acc_empty, (uint32_t)(chunk - 1) & 1u, g.err)) break;
+                if (!mbar_wait(&full[st], ph, g.err)) break;
+                tc_fence_after();
+                const uint32_t sa = base + (uint32_t)st * g.stage_bytes;
+                const uint32_t sb = sa + g.a_bytes;
+                for (int h = 0; h < 2; ++h) {  // two K=16 halves, 32 bytes apart in the 64-byte row
+                    const uint32_t restart = (first && h == 0) ? 0u : 1u;
+                    tc_mma(tmem, sw64_desc(sa + h * 32), sw64_desc(sb + h * 32), idesc, restart);
+                    tc_mma(tmem + BN, sw64_desc(sa + h * 32), sw64_desc(sb + BN * 64 + h * 32), idesc, restart);
+                    tc_mma(tmem + BN, sw64_desc(sa + BM * 64 + h * 32), sw64_desc(sb + h * 32), idesc, 1u);
+                    bool first2 = (i == 0 && h == 0);
+                    for (int L = 2; L < g.s; ++L)
+                        for (int t = 0; t <= L; ++t) {
+                            tc_mma(tmem + 2 * BN, sw64_desc(sa + t * (BM * 64) + h * 32),
+                                   sw64_desc(sb + (L - t) * (BN * 64) + h * 32), idesc, first2 ? 0u : 1u);
+                            first2 = false;
+                        }
+                }
+                tc_commit(&empty[st]);
+                if (last) tc_commit(acc_full);
+            }
+            // every MMA issued by this thread completes before TMEM is freed
+            tc_commit(drain);
+            const long long t0 = clock64();
+            while (!mbar_try_wait(drain, 0u) && clock64() - t0 < 2000000000ll) {
+            }
+        }
+    } else {
+        // ---------------- epilogue: warps 0..11 ----------------
+        const int q = warp & 3, grp = warp >> 2;
+        const uint32_t lane_addr = tmem + ((uint32_t)(q * 32) << 16);
+        int S0[NBG][16], S1[NBG][16];
+        float F[NBG][16];
+#pragma unroll
+        for (int jb = 0; jb < NBG; ++jb)
+#pragma unroll
+            for (int j = 0; j < 16; ++j) S0[jb][j] = S1[jb][j] = 0, F[jb][j] = 0.f;
+        bool ok = true;
+        for (int c = 0; c < nchunks; ++c) {
+            if (!mbar_wait(acc_full, (uint32_t)c & 1u, g.err)) {
+                ok = false;
+                break;
+            }
+            tc_fence_after();
+#pragma unroll
+            for (int jb = 0; jb < NBG; ++jb) {
+                const int b = grp + 3 * jb;
+                if (b < NB16) {
+                    uint32_t r0[16], r1[16];
+                    tc_ld16(lane_addr + b * 16, r0);
+                    tc_ld16(lane_addr + BN + b * 16, r1);
+                    tc_wait_ld();
+#pragma unroll
+                    for (int j = 0; j < 16; ++j) {
+                        S0[jb][j] += __float2int_rn(__uint_as_float(r0[j]));
+                        S1[jb][j] += __float2int_rn(__uint_as_float(r1[j]) * 256.0f);
+                    }
+                    if (c == nchunks - 1 && g.s > 2) {
+                        uint32_t r2[16];
+                        tc_ld16(lane_addr + 2 * BN + b * 16, r2);
+                        tc_wait_ld();
+#pragma unroll
+                        for (int j = 0; j < 16; ++j) F[jb][j] = __uint_as_float(r2[j]);
+                    }
+                }
+            }
+            tc_fence_before();
+            __syncwarp();
+            if (lane == 0) mbar_arrive(acc_empty);
+        }
+        if (ok) {
+            const int m = m0 + q * 32 + lane;
+            const int ea = (g.direct && m < g.M) ? g.eA[m] : 0;
+#pragma unroll
+            for (int jb = 0; jb < NBG; ++jb) {
+                const int b = grp + 3 * jb;
+                if (b >= NB16) continue;
+                if (g.direct) {
+                    if (m >= g.M) continue;
+#pragma unroll
+                    for (int j = 0; j < 16; ++j) {
+                        const int n = n0 + b * 16 + j;
+                        if (n >= g.N) continue;
+                        double v = (double)S0[jb][j] + ldexp((double)S1[jb][j], -8) + (double)F[jb][j];
+                        v = g.alpha * ldexp(v, ea + g.eB[n] - 16);
+                        double* cp = g.C + (size_t)m * g.ldc + n;
+                        *cp = (g.beta == 0.0) ? v : fma(g.beta, *cp, v);
+                    }
+                } else {
+                    const size_t row = ((size_t)blockIdx.z * g.Mpad + m) * g.Npad + n0 + b * 16;
+#pragma unroll
+                    for (int j = 0; j < 16; ++j) {
+                        g.PS0[row + j] = S0[jb][j];
+                        g.PS1[row + j] = S1[jb][j];
+                        g.PF[row + j] = F[jb][j];
+                    }
+                }
+            }
+        }
+    }
+    tc_fence_before();
+    __syncthreads();
+    if (warp == 0) {
+        tc_fence_after();
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(TMEM_COLS) : "memory");
+    }
+}
+
+// split-K partials -> C
+__global__ void k_oz_combine(const int* __restrict__ PS0, const int* __restrict__ PS1, const float* __restrict__ PF,
+                             int splits, int Mpad, int Npad, int M, int N, const int* __restrict__ eA,
+                             const int* __restrict__ eB, double alpha, double beta, double* __restrict__ C,
+                             int ldc) {
+    const size_t total = (size_t)M * N;
+    for (size_t t = blockIdx.x * (size_t)blockDim.x + threadIdx.x; t < total; t += (size_t)gridDim.x * blockDim.x) {
+        const int m = (int)(t / N), n = (int)(t % N);
+        long long s0 = 0, s1 = 0;
+        double f = 0.0;
+        for (int z = 0; z < splits; ++z) {
+            const size_t idx = ((size_t)z * Mpad + m) * Npad + n;
+            s0 += PS0[idx];
+            s1 += PS1[idx];
+            f += (double)PF[idx];
+        }
+        double v = (double)s0 + ldexp((double)s1, -8) + f;
+        v = alpha * ldexp(v, eA[m] + eB[n] - 16);
+        double* cp = C + (size_t)m * ldc + n;
+        *cp = (beta == 0.0) ? v : fma(beta, *cp, v);
+    }
+}
+
+}  // namespace oz
+}  // namespace ctm
+
+// ===========================================================================
+// host side
+// ===========================================================================
+namespace ctm {
+namespace {
+
+inline size_t align256(size_t b) { return (b + 255) & ~(size_t)255; }
+inline int k8_of(int K) { return (K + 7) & ~7; }
+
+PFN_cuTensorMapEncodeTiled_v12000 tmap_encoder() {
+    static PFN_cuTensorMapEncodeTiled_v12000 fn = nullptr;
+    static std::once_flag once;
+    std::call_once(once, [] {
+        void* p = nullptr;
+        cudaDriverEntryPointQueryResult q;
+        if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault, &q) ==
+                cudaSuccess &&
+            q == cudaDriverEntryPointSuccess)
+            fn = (PFN_cuTensorMapEncodeTiled_v12000)p;
+    });
+    return fn;
+}
+
+// slices [s][R][K8] bf16, 64-byte-swizzled boxes of {32, rows, s}
+bool make_map(CUtensorMap* map, const void* slices, int R, int K8, int s, int box_rows) {
+    auto enc = tmap_encoder();
+    if (!enc) return false;
+    const cuuint64_t dims[3] = {(cuuint64_t)K8, (cuuint64_t)R, (cuuint64_t)s};
+    const cuuint64_t strides[2] = {(cuuint64_t)K8 * 2, (cuuint64_t)R * K8 * 2};
+    const cuuint32_t box[3] = {(cuuint32_t)oz::BK, (cuuint32_t)box_rows, (cuuint32_t)s};
+    const cuuint32_t estr[3] = {1, 1, 1};
+    return enc(map, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 3, const_cast<void*>(slices), dims, strides, box, estr,
+               CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_64B, CU_TENSOR_MAP_L2_PROMOTION_L2_128B,
+               CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
+}
+
+struct Plan {
+    int nb16, bn, m_tiles, n_tiles, ksplit, kb_per_split, nkb, stages;
+    uint32_t a_bytes, stage_bytes;
+    size_t smem, ws_bytes;
+};
+
+Plan plan_of(int M, int N, int K, int s) {
+    Plan p{};
+    p.nb16 = N <= 144 ? (N + 15) / 16 : 8;
+    if (p.nb16 < 1) p.nb16 = 1;
+    p.bn = 16 * p.nb16;
+    p.m_tiles = (M + oz::BM - 1) / oz::BM;
+    p.n_tiles = (N + p.bn - 1) / p.bn;
+    p.nkb = (k8_of(K) + oz::BK - 1) / oz::BK;
+    if (p.nkb < 1) p.nkb = 1;
+    const int nchunks = (p.nkb + oz::CHUNK_KB - 1) / oz::CHUNK_KB;
+    const int tiles = p.m_tiles * p.n_tiles;
+    int ks = 1;
+    if (tiles < 120 && nchunks >= 2) ks = std::min(nchunks, (148 + tiles - 1) / tiles);
+    // int32 level sums stay exact for K <= 16384 per split
+    const int max_chunks_per_split = 16384 / (oz::CHUNK_KB * oz::BK);
+    ks = std::max(ks, (nchunks + max_chunks_per_split - 1) / max_chunks_per_split);
+    const int cps = (nchunks + ks - 1) / ks;
+    p.kb_per_split = cps * oz::CHUNK_KB;
+    p.ksplit = (p.nkb + p.kb_per_split - 1) / p.kb_per_split;
+    p.a_bytes = (uint32_t)(s * oz::BM * oz::BK * 2);
+    p.stage_bytes = p.a_bytes + (uint32_t)(s * p.bn * oz::BK * 2);
+    p.stages = std::min<int>(6, (int)((220u * 1024u) / p.stage_bytes));
+    p.smem = (size_t)p.stages * p.stage_bytes + 1024 + 256;
+    p.ws_bytes = p.ksplit > 1 ? 3 * align256((size_t)p.ksplit * p.m_tiles * oz::BM * p.n_tiles * p.bn * 4) : 0;
+    return p;
+}
+
+template <int NB16>
+cudaError_t launch_gemm(const Plan& p, const CUtensorMap& ta, const CUtensorMap& tb, const oz::GemmArgs& g,
+                        cudaStream_t st) {
+    static bool attr = false;
+    if (!attr) {
+        cudaError_t e = cudaFuncSetAttribute(oz::k_oz_gemm<NB16>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                             227 * 1024);
+        if (e != cudaSuccess) return e;
+        attr = true;
+    }
+    dim3 grid(p.m_tiles, p.n_tiles, p.ksplit);
+    ++g_launches;
+    oz::k_oz_gemm<NB16><<<grid, oz::THREADS, p.smem, st>>>(ta, tb, g);
+    return cudaGetLastError();
+}
+
+}  // namespace
+
+// split buffer: slices [s][R][K8] | row max bits [R] (u64) | exponents [R] (int)
+size_t oz_split_bytes(int R, int K, int s) {
+    return align256((size_t)s * R * k8_of(K) * 2) + align256((size_t)R * 8) + align256((size_t)R * 4);
+}
+inline const int* split_exponents(const void* buf, int R, int K8, int s) {
+    return (const int*)((const char*)buf + align256((size_t)s * R * K8 * 2) + align256((size_t)R * 8));
+}
+
+cudaError_t oz_split(const double* X, int R, int K, long long rs, long long cs, int s, void* buf, cudaStream_t st) {
+    if (R <= 0 || K <= 0 || s < 2 || s > oz::MAX_S) return cudaErrorInvalidValue;
+    const int K8 = k8_of(K);
+    __nv_bfloat16* sl = (__nv_bfloat16*)buf;
+    unsigned long long* mb = (unsigned long long*)((char*)buf + align256((size_t)s * R * K8 * 2));
+    int* ex = const_cast<int*>(split_exponents(buf, R, K8, s));
+    if (cs == 1) {
+        ++g_launches;
+        const unsigned blocks = (unsigned)(((size_t)R * 32 + 255) / 256);
+        oz::k_split_rows<<<blocks, 256, 0, st>>>(X, R, K, K8, rs, s, sl, ex);
+    } else {
+        cudaError_t e = cudaMemsetAsync(mb, 0, (size_t)R * 8, st);
+        if (e != cudaSuccess) return e;
+        const unsigned rg = (unsigned)((R + 31) / 32);
+        const unsigned kr = (unsigned)((K + oz::COLS_KRANGE - 1) / oz::COLS_KRANGE);
+        if ((kr + 3) / 4 > 65535u || (K8 / 32 + 2) / 2 > 65535) return cudaErrorInvalidValue;
+        ++g_launches;
+        oz::k_rowmax_cols<<<dim3(rg, (kr + 3) / 4), 128, 0, st>>>(X, R, K, rs, cs, mb);
+        ++g_launches;
+        oz::k_split_cols<<<dim3(rg, (unsigned)((K8 / 32 + 1 + 1) / 2)), 64, 0, st>>>(X, R, K, K8, rs, cs, s, mb, sl, ex);
+    }
+    return cudaGetLastError();
+}
+
+size_t oz_gemm_ws_bytes(int M, int N, int K, int s) { return plan_of(M, N, K, s).ws_bytes; }
+
+cudaError_t oz_gemm(int M, int N, int K, int s, const void* Asplit, const void* Bsplit, double alpha, double beta,
+                    double* C, int ldc, void* ws, size_t ws_bytes, int* err, cudaStream_t st) {
+    if (M <= 0 || N <= 0) return cudaSuccess;
+    if (K <= 0 || s < 2 || s > oz::MAX_S) return cudaErrorInvalidValue;
+    const Plan p = plan_of(M, N, K, s);
+    if (p.stages < 2 || p.ws_bytes > ws_bytes) return cudaErrorInvalidValue;
+    const int K8 = k8_of(K);
+    CUtensorMap ta, tb;
+    if (!make_map(&ta, Asplit, M, K8, s, oz::BM) || !make_map(&tb, Bsplit, N, K8, s, p.bn))
+        return cudaErrorInvalidValue;
+    oz::GemmArgs g{};
+    g.M = M;
+    g.N = N;
+    g.nkb = p.nkb;
+    g.kb_per_split = p.kb_per_split;
+    g.s = s;
+    g.stages = p.stages;
+    g.a_bytes = p.a_bytes;
+    g.stage_bytes = p.stage_bytes;
+    g.eA = split_exponents(Asplit, M, K8, s);
+    g.eB = split_exponents(Bsplit, N, K8, s);
+    g.direct = p.ksplit == 1;
+    g.alpha = alpha;
+    g.beta = beta;
+    g.C = C;
+    g.ldc = ldc;
+    g.Mpad = p.m_tiles * oz::BM;
+    g.Npad = p.n_tiles * p.bn;
+    if (!g.direct) {
+        const size_t part = align256((size_t)p.ksplit * g.Mpad * g.Npad * 4);
+        g.PS0 = (int*)ws;
+        g.PS1 = (int*)((char*)ws + part);
+        g.PF = (float*)((char*)ws + 2 * part);
+    }
+    g.err = err;
+    cudaError_t e;
+    switch (p.nb16) {
+        case 1: e = launch_gemm<1>(p, ta, tb, g, st); break;
+        case 2: e = launch_gemm<2>(p, ta, tb, g, st); break;
+        case 3: e = launch_gemm<3>(p, ta, tb, g, st); break;
+        case 4: e = launch_gemm<4>(p, ta, tb, g, st); break;
+        case 5: e = launch_gemm<5>(p, ta, tb, g, st); break;
+        case 6: e = launch_gemm<6>(p, ta, tb, g, st); break;
+        case 7: e = launch_gemm<7>(p, ta, tb, g, st); break;
+        case 8: e = launch_gemm<8>(p, ta, tb, g, st); break;
+        default: e = launch_gemm<9>(p, ta, tb, g, st); break;
+    }
+    if (e != cudaSuccess || g.direct) return e;
+    size_t blocks = ((size_t)M * N + 255) / 256;
+    if (blocks > 152 * 16) blocks = 152 * 16;
+    ++g_launches;
+    oz::k_oz_combine<<<(unsigned)blocks, 256, 0, st>>>(g.PS0, g.PS1, g.PF, p.ksplit, g.Mpad, g.Npad, M, N, g.eA,
+                                                        g.eB, alpha, beta, C, ldc);
+    return cudaGetLastError();
+}
+
+}  // namespace ctm

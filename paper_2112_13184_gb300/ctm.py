@@ -78,6 +78,9 @@ _sig("ctm_qr", c_int, c_void_p, c_int, c_int, c_void_p, c_void_p, c_void_p, c_vo
 _sig("ctm_svd_workspace_bytes", c_size_t, c_int)
 _sig("ctm_svd", c_int, c_void_p, c_int, c_void_p, c_void_p, c_void_p, c_void_p, c_void_p)
 
+_sig("ctm_gemm_ozaki_workspace_bytes", c_size_t, c_int, c_int, c_int, c_int)
+_sig("ctm_gemm_ozaki", c_int, c_int, c_int, c_int, c_int, c_int, c_double, c_void_p, c_int, c_void_p, c_int,
+     c_double, c_void_p, c_int, c_int, c_void_p, c_void_p)
 _sig("ctm_svd_noalloc", c_int, c_void_p, c_int, c_void_p, c_void_p, c_void_p, c_void_p)
 _sig("ctm_profile_enable", c_int, c_void_p, c_int)
 _sig("ctm_profile_read", c_int, c_void_p, ctypes.POINTER(ctm_profile_data), c_int)
@@ -273,6 +276,15 @@ def ctm_svd_workspace_bytes(k):
 def ctm_svd(G, k, U, S, V, ws, stream=None):
     _check(_lib.ctm_svd(_dev_ptr(G), k, _dev_ptr(U), _dev_ptr(S), _dev_ptr(V), ctypes.c_void_p(ws.data_ptr()),
                         _stream_ptr(stream)))
+
+
+def ctm_gemm_ozaki_workspace_bytes(M, N, K, slices):
+    return _lib.ctm_gemm_ozaki_workspace_bytes(M, N, K, slices)
+
+
+def ctm_gemm_ozaki(transA, transB, M, N, K, alpha, A, lda, B, ldb, beta, C, ldc, slices, ws, stream=None):
+    _check(_lib.ctm_gemm_ozaki(int(transA), int(transB), M, N, K, alpha, _dev_ptr(A), lda, _dev_ptr(B), ldb,
+                               beta, _dev_ptr(C), ldc, slices, ctypes.c_void_p(ws.data_ptr()), _stream_ptr(stream)))
 
 
 def ctm_svd_noalloc(G, k, U, S, V, stream=None):

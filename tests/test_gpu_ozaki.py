@@ -1,0 +1,102 @@
+"""Emulated-FP64 tensor-core GEMM (ctm_gemm_ozaki) against numpy FP64.
+
+Exactness pins: when every operand entry is a whole number of the slice
+unit (integers below 2^8 of the row/column maximum use only the leading
+digit; below 2^16 only the two leading digits), every slice product the
+kernel keeps is accumulated exactly (levels 0 and 1), nothing is dropped,
+and the FP64 result must equal numpy's bit for bit (all partial sums stay
+far below 2^53).  Shapes cross the 128-row and 16..144-column tiles with
+ragged tails, several 256-wide K chunks, split-K and both transposes.
+General data: error within the slicing bound 2^(2-8s) max|row| max|col| K.
+"""
+import numpy as np
+import pytest
+
+pytestmark = pytest.mark.gpu
+torch = pytest.importorskip("torch")
+
+
+@pytest.fixture(scope="module")
+def ctm():
+    if not torch.cuda.is_available():
+        pytest.skip("no GPU")
+    from paper_2112_13184_gb300 import ctm as m
+    return m
+
+
+def run(ctm, A, B, tA, tB, slices, alpha=1.0, beta=0.0, C0=None):
+    M = A.shape[1] if tA else A.shape[0]
+    K = A.shape[0] if tA else A.shape[1]
+    N = B.shape[0] if tB else B.shape[1]
+    dA = torch.from_numpy(np.ascontiguousarray(A)).cuda()
+    dB = torch.from_numpy(np.ascontiguousarray(B)).cuda()
+    dC = torch.from_numpy(np.ascontiguousarray(C0 if C0 is not None else np.zeros((M, N)))).cuda()
+    ws = torch.zeros(ctm.ctm_gemm_ozaki_workspace_bytes(M, N, K, slices), dtype=torch.uint8, device="cuda")
+    ctm.ctm_gemm_ozaki(tA, tB, M, N, K, alpha, dA, A.shape[1], dB, B.shape[1], beta, dC, N, slices, ws)
+    torch.cuda.synchronize()
+    assert int(ws[:4].view(torch.int32).item()) == 0, "a bounded device wait gave up"
+    return dC.cpu().numpy()
+
+
+SHAPES = [(128, 16, 32), (200, 144, 1000), (129, 33, 300), (64, 64, 64), (300, 200, 520), (1, 1, 1),
+          (257, 100, 2048)]
+
+
+@pytest.mark.parametrize("M,N,K", SHAPES)
+@pytest.mark.parametrize("tA,tB", [(0, 0), (1, 0), (0, 1), (1, 1)])
+def test_exact_leading_digit(ctm, M, N, K, tA, tB):
+    rng = np.random.default_rng(M + 3 * N + 7 * K + tA + 2 * tB)
+    A = rng.integers(-255, 256, size=(K, M) if tA else (M, K)).astype(np.float64)
+    B = rng.integers(-255, 256, size=(N, K) if tB else (K, N)).astype(np.float64)
+    ref = (A.T if tA else A) @ (B.T if tB else B)
+    got = run(ctm, A, B, tA, tB, slices=3)
+    np.testing.assert_array_equal(got, ref)
+
+
+@pytest.mark.parametrize("M,N,K", [(200, 144, 1000), (300, 200, 520), (257, 100, 2048)])
+def test_exact_two_digits(ctm, M, N, K):
+    """A uses one digit, B two (integers below 2^16 with a row maximum near
+    2^16): the level-1 accumulator is exercised and stays exact."""
+    rng = np.random.default_rng(K)
+    A = rng.integers(-255, 256, size=(M, K)).astype(np.float64)
+    B = rng.integers(-65535, 65536, size=(K, N)).astype(np.float64)
+    B[0, :] = 65535.0  # pin every column maximum just below 2^16
+    ref = A @ B
+    got = run(ctm, A, B, 0, 0, slices=2)
+    np.testing.assert_array_equal(got, ref)
+
+
+@pytest.mark.parametrize("slices", [3, 4, 5])
+@pytest.mark.parametrize("M,N,K", [(200, 144, 1000), (300, 200, 520)])
+def test_random_within_slicing_bound(ctm, slices, M, N, K):
+    rng = np.random.default_rng(slices * 100 + M)
+    A = rng.standard_normal((M, K)) * np.logspace(0, -6, M)[:, None]
+    B = rng.standard_normal((K, N)) * np.logspace(0, -6, N)[None, :]
+    ref = A @ B
+    got = run(ctm, A, B, 0, 0, slices)
+    bound = 2.0 ** (2 - 8 * slices) * np.abs(A).max(axis=1)[:, None] * np.abs(B).max(axis=0)[None, :] * K
+    assert np.all(np.abs(got - ref) <= bound)
+
+
+def test_alpha_beta(ctm):
+    rng = np.random.default_rng(5)
+    A = rng.integers(-100, 100, size=(70, 90)).astype(np.float64)
+    B = rng.integers(-100, 100, size=(90, 40)).astype(np.float64)
+    C0 = rng.integers(-100, 100, size=(70, 40)).astype(np.float64)
+    got = run(ctm, A, B, 0, 0, 3, alpha=2.0, beta=-0.5, C0=C0)
+    np.testing.assert_array_equal(got, 2.0 * (A @ B) - 0.5 * C0)
+
+
+def test_corner_apply_shape(ctm):
+    """The projector's corner apply at D=8, chi=128: 8192 x 8192 times 8192 x 144."""
+    N, k = 8192, 144
+    g = torch.Generator(device="cuda").manual_seed(0)
+    E = torch.randn(N, N, dtype=torch.float64, device="cuda", generator=g)
+    X = torch.randn(N, k, dtype=torch.float64, device="cuda", generator=g)
+    Y = torch.empty(N, k, dtype=torch.float64, device="cuda")
+    ws = torch.zeros(ctm.ctm_gemm_ozaki_workspace_bytes(N, k, N, 4), dtype=torch.uint8, device="cuda")
+    ctm.ctm_gemm_ozaki(0, 0, N, k, N, 1.0, E, N, X, k, 0.0, Y, k, 4, ws)
+    ref = E @ X
+    torch.cuda.synchronize()
+    err = (Y - ref).abs().max().item()
+    assert err < 2.0 ** -30 * E.abs().max().item() * X.abs().max().item() * N

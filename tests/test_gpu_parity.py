@@ -79,6 +79,23 @@ def test_neel_d2_D3_chi16_randomised_svd(ctm):
     c.close()
 
 
+@pytest.mark.parametrize("slices,tol", [(5, 1e-8), (6, 1e-8), (4, 1e-7)])
+def test_neel_d2_D3_chi16_emulated_fp64(ctm, slices, tol):
+    """Every contraction on the tensor cores as BF16 slice products (QR, SVD
+    and normalisation in FP64): the energy of every bond and every <Sz> stays
+    within |dE| <= 1e-8 of the FP64 oracle from 5 slices on; 4 slices sit at
+    the 1e-8 level."""
+    w = I.workload("neel_d2_D3_chi16")
+    c, ref = run_both(ctm, w["As"], w["envs"], w["d"], w["D"], w["chi"], w["sweeps"],
+                      precision=ctm.CTM_OZAKI_BF16, ozaki_slices=slices)
+    g = observables_gpu(c, w["op1"], w["op2"])
+    o = observables_oracle(ref, w["As"], w["op1"], w["op2"])
+    err = np.abs(g - o)
+    print(f"slices={slices}: max |dO| = {err.max():.3e} per observable {err}")
+    assert err.max() < tol, err
+    c.close()
+
+
 # Converged, well-posed cases (sigma_chi / sigma_0 of M >= 3e-7, the oracle
 # converges to < 1e-12): N = chi D^2 = 81, 32, 90 cut across the 64-wide
 # GEMM tiles; d > D in the second.  Cases whose chi reaches the noise floor
