@@ -40,7 +40,8 @@ def parse():
     ap.add_argument("--steps", type=int, default=3)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--precision", default="fp64", choices=["fp64", "mixed"])
+    ap.add_argument("--precision", default="mixed", choices=["fp64", "mixed"])
+    ap.add_argument("--slices", type=int, default=5)
     ap.add_argument("--workload", default="xpol_d3_D8_chi128", choices=sorted(WORKLOADS))
     ap.add_argument("--e2e-steps", type=int, default=1)
     ap.add_argument("--no-cpu-baseline", action="store_true")
@@ -166,7 +167,7 @@ def run_ours(args):
     d, D, chi = w["d"], w["D"], w["chi"]
     prec = C.CTM_OZAKI_BF16 if args.precision == "mixed" else C.CTM_FP64
     stream = torch.cuda.Stream()
-    solver = C.CTMRG(d, D, chi, stream=stream, precision=prec, seed=rank)
+    solver = C.CTMRG(d, D, chi, stream=stream, precision=prec, seed=rank, ozaki_slices=args.slices)
     solver.set_tensors(w["As"])
     solver.set_envs(w["envs"])
 
@@ -175,12 +176,9 @@ def run_ours(args):
         if world > 1:
             torch.distributed.barrier()
 
-    # warm-up
+    # warm-up (the first sweep is eager; warm sweeps replay one CUDA graph)
     solver.sweep(args.warmup)
     # timed: K sweeps on the handle's stream, inputs resident in HBM
-    C.ctm_profile_enable(solver.h, True)
-    C.ctm_profile_read(solver.h, reset=True)
-    launches0 = C.ctm_kernel_launches()
     barrier()
     ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     with ClockSampler(local) as clk:
@@ -188,10 +186,18 @@ def run_ours(args):
         solver.sweep(args.steps)
         ev1.record(stream)
         barrier()
-    launches = C.ctm_kernel_launches() - launches0
+    ms = ev0.elapsed_time(ev1)
+    # kernels launched per sweep: counted on one eager, event-timed sweep
+    # (graph replays launch the same kernels without host calls); the same
+    # sweep gives the per-class device times for the roofline
+    C.ctm_profile_enable(solver.h, True)
+    C.ctm_profile_read(solver.h, reset=True)
+    l0 = C.ctm_kernel_launches()
+    solver.sweep(1)
+    launches = (C.ctm_kernel_launches() - l0) * args.steps
+    by_op = C.ctm_profile_report(solver.h)
     prof = C.ctm_profile_read(solver.h, reset=True)
     C.ctm_profile_enable(solver.h, False)
-    ms = ev0.elapsed_time(ev1)
     t = torch.tensor([ms], device="cuda")
     if world > 1:
         torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
@@ -227,6 +233,8 @@ def run_ours(args):
     if rank == 0:
         g = prof["gemm"]
         achieved = g["flops"] / (g["ms"] / 1e3) / 1e12 if g["ms"] > 0 else None
+        prof_note = ("per-class device time of one eager sweep with CUDA events around every call, "
+                     "run right after the timed region (graph replays cannot be timed per kernel)")
         if prec == C.CTM_FP64:
             roof = {"bound": "alu", "kernel": "k_dgemm (FP64 DFMA)", "achieved": achieved,
                     "peak": FP64_NOMINAL_TFLOPS, "unit": "TFLOP/s",
@@ -235,7 +243,8 @@ def run_ours(args):
         else:
             peaks = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
             pk = peaks["bf16_tflops_sustained"]
-            roof = {"bound": "tensor", "kernel": "ozaki bf16 tcgen05 GEMM", "achieved": achieved, "peak": pk,
+            roof = {"bound": "tensor", "kernel": "k_oz_gemm (tcgen05 BF16 slice products)", "achieved": achieved,
+                    "peak": pk,
                     "unit": "TFLOP/s", "frac": achieved / pk if achieved else None, "traffic": None,
                     "peak_source": "MEASURED_PEAKS.json bf16_tflops_sustained (of measured)"}
         total_ms = sum(p["ms"] for p in prof.values())
@@ -245,6 +254,7 @@ def run_ours(args):
             "scaling": "weak", "vs_baseline": None, "dtype": "f64" if prec == C.CTM_FP64 else "bf16x-slices->f64",
             "data": "synthetic",
             "config": {"workload": args.workload, "desc": WORKLOADS[args.workload], "precision": args.precision,
+                       "slices": args.slices if prec != C.CTM_FP64 else None,
                        "parallelism": f"replicas x{world}",
                        "l2": "working set per sweep (N x N corners, 537 MB each) exceeds the 129 MB L2"},
             "roofline": roof,
@@ -252,6 +262,9 @@ def run_ours(args):
                     "d2h_bytes_per_step": d2h, "steps": args.e2e_steps},
             "gpu_launches": launches,
             "clocks": clk.summary(),
+            "profile_note": prof_note,
+            "profile_by_op": {k: {"ms": round(v["ms"], 3), "calls": v["calls"]} for k, v in
+                              sorted(by_op.items(), key=lambda kv: -kv[1]["ms"])},
             "profile": {k: {"ms": round(v["ms"], 3), "share": round(v["ms"] / total_ms, 4) if total_ms else None,
                             "calls": v["calls"], "tflops": (v["flops"] / (v["ms"] / 1e3) / 1e12)
                             if v["ms"] > 0 and v["flops"] > 0 else None}

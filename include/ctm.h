@@ -85,11 +85,15 @@ typedef struct {
     uint64_t seed;          /* counter-based RNG seed for the rSVD test matrices   */
     int exact_svd_max_n;    /* N = chi*D*D <= this: k = N, the range finder spans
                                everything and the truncated SVD is exact           */
+    int rsvd_warm_start;    /* != 0: after the first sweep each cut's range finder
+                               starts from that cut's basis of the previous sweep
+                               (one subspace iteration per sweep, no extra power
+                               iterations); reset by ctm_set_tensor / ctm_set_env */
 } ctm_options;
 
 /* Defaults: chi=16, max_sweeps=100, tol=1e-10, FP64, 5 slices,
  * p=max(8,chi/8) (when rsvd_oversample<=0), q=2, cutoff 1e-12, seed 0,
- * exact_svd_max_n=256. */
+ * exact_svd_max_n=256, rsvd_warm_start=1. */
 ctm_status ctm_default_options(ctm_options* opt);
 
 /* Device bytes a handle of this shape allocates (workspace included). */
@@ -143,15 +147,23 @@ const char* ctm_status_string(ctm_status s);
  * events on its stream; ctm_profile_read returns the accumulated device
  * time per class together with the algorithmic FLOPs (2MNK per GEMM) and
  * bytes (read + write per permutation) of the calls timed.  Classes:
- * 0 GEMM, 1 permute, 2 QR, 3 SVD.  reset != 0 zeroes the counters. */
+ * 0 GEMM (FP64 DFMA or tensor-core slice products), 1 permute, 2 QR, 3 SVD,
+ * 4 operand slicing of the emulated GEMM, 5..7 unused.  reset != 0 zeroes
+ * the counters. */
 typedef struct {
-    double ms[4];
-    double flops[4];
-    double bytes[4];
-    long long calls[4];
+    double ms[8];
+    double flops[8];
+    double bytes[8];
+    long long calls[8];
 } ctm_profile_data;
 ctm_status ctm_profile_enable(ctm_handle h, int on);
 ctm_status ctm_profile_read(ctm_handle h, ctm_profile_data* out, int reset);
+
+/* The same timings broken down by operation (enlarged corner products X2,
+ * X3, X4, range-finder and projector applies, absorption, QR, SVD) and
+ * class, as a JSON object written to buf (len bytes including the NUL;
+ * CTM_ERR_ARG if it does not fit). */
+ctm_status ctm_profile_report(ctm_handle h, char* buf, size_t len, int reset);
 
 /* Number of CUDA kernels libctm has launched in this process (all handles
  * and kernel-level calls); cudaMemset/cudaMemcpy are not counted. */

@@ -19,6 +19,8 @@
 
 #include <algorithm>
 #include <array>
+#include <map>
+#include <set>
 #include <cmath>
 #include <cstdio>
 #include <cstring>
@@ -80,6 +82,9 @@ struct ctm_ctx {
     double *Om = nullptr, *Yb = nullptr, *Zb = nullptr, *Qm = nullptr, *Qm2 = nullptr, *Qb = nullptr;
     double *Rb = nullptr, *G = nullptr, *Us = nullptr, *Ws = nullptr, *Sv = nullptr, *inv = nullptr;
     double *Uc = nullptr, *Vc = nullptr, *t1 = nullptr, *t2 = nullptr;
+    // Cholesky-QR scratch (k x k) and the first-pass basis (N x k)
+    double *cq_G = nullptr, *cq_R1 = nullptr, *cq_R1i = nullptr, *cq_R2 = nullptr, *cq_R2i = nullptr,
+           *cq_d = nullptr, *cq_Q1 = nullptr;
     double *newC1 = nullptr, *newC4 = nullptr, *newT4 = nullptr, *tmpT = nullptr;
     double *Lh = nullptr, *Rh = nullptr, *rho = nullptr, *spec = nullptr, *corners = nullptr;
     double* splitk = nullptr;  // split-K partial sums
@@ -87,14 +92,28 @@ struct ctm_ctx {
     // emulated-FP64 tensor-core GEMMs: operand slices and split-K partials
     void *ozA = nullptr, *ozB = nullptr, *ozW = nullptr;
     size_t ozA_n = 0, ozB_n = 0, ozW_n = 0;
+    // slices of the four enlarged corners (x plain / transposed), reused by
+    // every corner apply of a cut; invalidated by any write to the corner
+    struct SliceCache { const double* ptr = nullptr; bool trans = false; void* buf = nullptr; bool valid = false; };
+    SliceCache ozc[8];
+    // warm start of the range finder: previous sweep's right basis per cut
+    double* warmV[16] = {};
+    bool warm_valid[16] = {};
+    // one warm sweep captured as a CUDA graph and replayed
+    cudaGraph_t graph = nullptr;
+    cudaGraphExec_t graph_exec = nullptr;
+    bool use_graphs = true;
     // optional per-class device timing (ctm_profile_*)
     bool prof = false;
     std::vector<cudaEvent_t> ev_pool;
     size_t ev_used = 0;
-    struct Rec { int cls; size_t ev; double flops, bytes; };
+    struct Rec { int cls; size_t ev; double flops, bytes; const char* tag; };
     std::vector<Rec> recs;
-    double p_ms[4] = {0, 0, 0, 0}, p_flops[4] = {0, 0, 0, 0}, p_bytes[4] = {0, 0, 0, 0};
-    long long p_calls[4] = {0, 0, 0, 0};
+    const char* tag = "other";  // label of the calls being issued (ProfTag)
+    struct TagAcc { double ms = 0, flops = 0, bytes = 0; long long calls = 0; };
+    std::map<std::string, TagAcc> tags;
+    double p_ms[8] = {}, p_flops[8] = {}, p_bytes[8] = {};
+    long long p_calls[8] = {};
     void* qr_ws = nullptr;
     void* svd_ws = nullptr;
     void* sval_ws = nullptr;
@@ -148,7 +167,8 @@ std::vector<std::array<long long, 3>> gemm_shapes(int d, int D, int chi, int k) 
     return {{chi, N, chi},      {N, N, chi},          {M3, d * D2, D2},     {M3, D2, d * D2},
             {M3 * d, d * D2, D2}, {N, k, N},          {N, chi, k},          {N, chi, N},
             {chi, chi, N},      {chi, N, N},          {N, chi, chi},        {N * D2, chi, chi},
-            {(long long)d * d, 1, N * N}, {N * d * d, chi, N}, {(long long)d * d, (long long)d * d, N * chi}};
+            {(long long)d * d, 1, N * N}, {N * d * d, chi, N}, {(long long)d * d, (long long)d * d, N * chi},
+            {k, k, N},          {N, k, k}};
 }
 
 struct OzBounds {
@@ -179,16 +199,18 @@ size_t footprint(int d, int D, const ctm_options& o) {
     dbl += 6 * z.Nk;                 // Om, Y, Z, Qm, Qm2, Qb
     dbl += 4 * z.kk + 2 * (size_t)k; // Rb, G, Us, Ws, Sv, inv
     dbl += 4 * z.Nchi;               // Uc, Vc, t1, t2
+    dbl += 5 * z.kk + k + z.Nk;      // Cholesky-QR scratch
     dbl += 2 * z.C + 2 * z.T;        // newC1, newC4, newT4, tmpT
     dbl += 2 * z.Nchi * d * d;       // Lh, Rh
     dbl += std::max<size_t>(64 * 64, (size_t)d * d * d * d) + 2 * 16 * z.C;  // rho, spectra, corners
     dbl += (size_t)1 << 24;          // split-K partials
+    if (o.rsvd_warm_start && k < N) dbl += 16 * z.Nk;  // warm-start bases
     size_t bytes = dbl * sizeof(double);
     bytes += qr_ws_bytes(N, k) + svd_ws_bytes(k) + svals_ws_bytes(chi, 16);
     bytes += 64 * sizeof(unsigned long long) + 64 + 64 * 256;
     if (o.precision == CTM_OZAKI_BF16) {
         const OzBounds z = oz_bounds(d, D, chi, k, o.ozaki_slices);
-        bytes += z.a + z.b + z.w + 3 * 256;
+        bytes += z.a + z.b + z.w + 3 * 256 + 8 * ctm::oz_split_bytes(N, N, o.ozaki_slices);
     }
     return bytes;
 }
@@ -211,7 +233,7 @@ ctm_status allocd(ctm_ctx* h, Tp** p, size_t n) {
 // ----------------------------------------------------------------------------
 // per-class device timing: an event pair around each call when enabled
 // ----------------------------------------------------------------------------
-enum { P_GEMM = 0, P_PERM = 1, P_QR = 2, P_SVD = 3 };
+enum { P_GEMM = 0, P_PERM = 1, P_QR = 2, P_SVD = 3, P_SPLIT = 4, P_NCLASS = 8 };
 constexpr size_t NO_EV = ~(size_t)0;
 
 size_t prof_begin(ctm_ctx* h) {
@@ -229,8 +251,19 @@ size_t prof_begin(ctm_ctx* h) {
 void prof_end(ctm_ctx* h, size_t i, int cls, double flops, double bytes) {
     if (i == NO_EV) return;
     cudaEventRecord(h->ev_pool[i + 1], h->stream);
-    h->recs.push_back({cls, i, flops, bytes});
+    h->recs.push_back({cls, i, flops, bytes, h->tag});
 }
+
+// labels every profiled call issued in its scope (nested scopes restore)
+struct ProfTag {
+    ctm_ctx* h;
+    const char* prev;
+    ProfTag(ctm_ctx* h_, const char* t) : h(h_), prev(h_->tag) {
+        static std::set<std::string> names;  // interned: records keep the pointer
+        h->tag = names.insert(t).first->c_str();
+    }
+    ~ProfTag() { h->tag = prev; }
+};
 void prof_collect(ctm_ctx* h) {
     if (h->recs.empty()) return;
     cudaStreamSynchronize(h->stream);
@@ -241,6 +274,12 @@ void prof_collect(ctm_ctx* h) {
         h->p_flops[r.cls] += r.flops;
         h->p_bytes[r.cls] += r.bytes;
         h->p_calls[r.cls] += 1;
+        static const char* cls_name[8] = {"gemm", "permute", "qr", "svd", "split", "c5", "c6", "c7"};
+        auto& t = h->tags[std::string(r.tag) + "/" + cls_name[r.cls]];
+        t.ms += ms;
+        t.flops += r.flops;
+        t.bytes += r.bytes;
+        t.calls += 1;
     }
     h->recs.clear();
     h->ev_used = 0;
@@ -249,9 +288,28 @@ void prof_collect(ctm_ctx* h) {
 // ----------------------------------------------------------------------------
 // contractions
 // ----------------------------------------------------------------------------
+void slices_written(ctm_ctx* h, const double* p) {
+    for (auto& c : h->ozc)
+        if (c.ptr == p) c.valid = false;
+}
+int slice_slot(ctm_ctx* h, const double* A, bool tA, int M, int K) {
+    if (!h->ozc[0].buf || M != h->N || K != h->N) return -1;
+    for (int c = 0; c < 4; ++c)
+        if (A == h->E[c]) return 2 * c + (tA ? 1 : 0);
+    return -1;
+}
+ctm_status split_(ctm_ctx* h, const double* X, int R, int K, long long rs, long long cs, void* dst) {
+    const size_t ev = prof_begin(h);
+    CK(ctm::oz_split(X, R, K, rs, cs, h->opt.ozaki_slices, dst, h->stream));
+    prof_end(h, ev, P_SPLIT, 0.0, (8.0 + 2.0 * h->opt.ozaki_slices) * (double)R * K);
+    return CTM_OK;
+}
+
 ctm_status gemm(ctm_ctx* h, bool tA, bool tB, int M, int N, int K, const double* A, int lda,
                 const double* B, int ldb, double* C, int ldc, double beta = 0.0) {
-    const size_t ev = prof_begin(h);
+    slices_written(h, C);
+    const double flops = 2.0 * M * N * K;
+    const double bytes = 8.0 * ((double)M * K + (double)K * N + (double)M * N);
     // a matrix-vector product gains nothing from 128-wide tensor tiles
     if (h->opt.precision == CTM_OZAKI_BF16 && M > 0 && N > 1 && K > 0) {
         const int s = h->opt.ozaki_slices;
@@ -261,32 +319,92 @@ ctm_status gemm(ctm_ctx* h, bool tA, bool tB, int M, int N, int K, const double*
             return CTM_ERR_STATE;
         }
         // op(A)[m][k] and op(B)[k][n] as row views of M x K and N x K
-        CK(ctm::oz_split(A, M, K, tA ? 1 : lda, tA ? lda : 1, s, h->ozA, h->stream));
-        CK(ctm::oz_split(B, N, K, tB ? ldb : 1, tB ? 1 : ldb, s, h->ozB, h->stream));
-        CK(ctm::oz_gemm(M, N, K, s, h->ozA, h->ozB, 1.0, beta, C, ldc, h->ozW, h->ozW_n, h->flag + 1, h->stream));
+        const int slot = slice_slot(h, A, tA, M, K);
+        void* sa = slot >= 0 ? h->ozc[slot].buf : h->ozA;
+        if (slot < 0 || !h->ozc[slot].valid) {
+            CKS(split_(h, A, M, K, tA ? 1 : lda, tA ? lda : 1, sa));
+            if (slot >= 0) h->ozc[slot].valid = true;
+        }
+        CKS(split_(h, B, N, K, tB ? ldb : 1, tB ? 1 : ldb, h->ozB));
+        const size_t ev = prof_begin(h);
+        CK(ctm::oz_gemm(M, N, K, s, sa, h->ozB, 1.0, beta, C, ldc, h->ozW, h->ozW_n, h->flag + 1, h->stream));
+        prof_end(h, ev, P_GEMM, flops, bytes);
     } else {
+        const size_t ev = prof_begin(h);
         CK(ctm::dgemm(tA, tB, M, N, K, 1.0, A, lda, B, ldb, beta, C, ldc, h->stream, h->splitk, h->splitk_n));
+        prof_end(h, ev, P_GEMM, flops, bytes);
     }
+    return CTM_OK;
+}
+// emulated GEMM on strided views: op(A) element (m, k) at A[view(ar, m) +
+// view(ak, k)], op(B) element (k, n) at B[view(bn, n) + view(bk, k)], C
+// element (m, n) written at C[view(cr, m) + view(cc, n)]
+ctm_status gemm_v(ctm_ctx* h, int M, int N, int K, const double* A, const OzView& ar, const OzView& ak,
+                  const double* B, const OzView& bn, const OzView& bk, double* C, const OzView& cr,
+                  const OzView& cc) {
+    slices_written(h, C);
+    const int s = h->opt.ozaki_slices;
+    if (ctm::oz_split_bytes(M, K, s) > h->ozA_n || ctm::oz_split_bytes(N, K, s) > h->ozB_n ||
+        ctm::oz_gemm_ws_bytes(M, N, K, s) > h->ozW_n) {
+        h->err = "emulated GEMM: shape outside the handle's workspace";
+        return CTM_ERR_STATE;
+    }
+    size_t ev = prof_begin(h);
+    CK(ctm::oz_split_view(A, M, K, ar, ak, s, h->ozA, h->stream));
+    prof_end(h, ev, P_SPLIT, 0.0, (8.0 + 2.0 * s) * (double)M * K);
+    ev = prof_begin(h);
+    CK(ctm::oz_split_view(B, N, K, bn, bk, s, h->ozB, h->stream));
+    prof_end(h, ev, P_SPLIT, 0.0, (8.0 + 2.0 * s) * (double)N * K);
+    ev = prof_begin(h);
+    CK(ctm::oz_gemm_view(M, N, K, s, h->ozA, h->ozB, 1.0, 0.0, C, cr, cc, h->ozW, h->ozW_n, h->flag + 1,
+                         h->stream));
     prof_end(h, ev, P_GEMM, 2.0 * M * N * K, 8.0 * ((double)M * K + (double)K * N + (double)M * N));
     return CTM_OK;
 }
+
 ctm_status perm(ctm_ctx* h, const double* src, double* dst, std::initializer_list<int> dims,
                 std::initializer_list<int> p) {
     std::vector<int> dv(dims), pv(p);
     double n = 1;
     for (int v : dv) n *= v;
+    slices_written(h, dst);
     const size_t ev = prof_begin(h);
     CK(ctm::permute(src, dst, (int)dv.size(), dv.data(), pv.data(), h->stream));
     prof_end(h, ev, P_PERM, 0.0, 16.0 * n);
     return CTM_OK;
 }
 ctm_status qr_(ctm_ctx* h, const double* Y, double* Q, double* R) {
+    ProfTag tg(h, "qr");
     const size_t ev = prof_begin(h);
     CK(ctm::qr(Y, h->N, h->k, Q, R, h->qr_ws, h->stream));
     prof_end(h, ev, P_QR, 4.0 * h->N * (double)h->k * h->k, 0.0);
     return CTM_OK;
 }
+// Column-equilibrated Cholesky QR, two passes (CholQR2): for the bases of a
+// warm-started range finder, whose columns are close to orthogonal with
+// graded norms, it is as accurate as Householder and is GEMM work.
+//   G = Y^T Y, D = diag(G)^1/2, D^-1 G D^-1 = R1'^T R1', Q1 = Y D^-1 R1'^-1,
+//   Q1^T Q1 = R2^T R2, Q = Q1 R2^-1, R = R2 R1' D.
+ctm_status qr_chol(ctm_ctx* h, const double* Y, double* Q, double* R) {
+    ProfTag tg(h, "qr");
+    const size_t ev = prof_begin(h);
+    const int N = h->N, k = h->k;
+    CKS(gemm(h, true, false, k, k, N, Y, k, Y, k, h->cq_G, k));
+    CK(ctm::equilibrate(h->cq_G, k, h->cq_d, h->stream));
+    CK(ctm::chol_inv(h->cq_G, k, 1e-14, h->cq_R1, h->cq_R1i, h->stream));
+    CK(ctm::scale_rc(h->cq_R1i, k, h->cq_d, true, true, h->stream));  // D^-1 R1'^-1
+    CKS(gemm(h, false, false, N, k, k, Y, k, h->cq_R1i, k, h->cq_Q1, k));
+    CKS(gemm(h, true, false, k, k, N, h->cq_Q1, k, h->cq_Q1, k, h->cq_G, k));
+    CK(ctm::chol_inv(h->cq_G, k, 0.0, h->cq_R2, h->cq_R2i, h->stream));
+    CKS(gemm(h, false, false, N, k, k, h->cq_Q1, k, h->cq_R2i, k, Q, k));
+    CK(ctm::scale_rc(h->cq_R1, k, h->cq_d, false, false, h->stream));  // R1' D
+    CK(ctm::dgemm(false, false, k, k, k, 1.0, h->cq_R2, k, h->cq_R1, k, 0.0, R, k, h->stream));
+    prof_end(h, ev, P_QR, 8.0 * N * (double)k * k, 0.0);
+    return CTM_OK;
+}
+
 ctm_status svd_(ctm_ctx* h) {
+    ProfTag tg(h, "svd");
     const size_t ev = prof_begin(h);
     CK(ctm::svd(h->G, h->k, h->Us, h->Sv, h->Ws, h->svd_ws, h->stream));
     prof_end(h, ev, P_SVD, 0.0, 0.0);
@@ -301,7 +419,35 @@ ctm_status corner_core(ctm_ctx* h, const double* X1, const double* Tp, const dou
     const int chi = h->chi, D = h->D, d = h->d, N = h->N;
     const int D2 = D * D;
     // X2[(a,l,l'), (u,u',b)] = Tp[(a,l,l'), g] X1[g, (u,u',b)]
-    CKS(gemm(h, false, false, N, N, chi, Tp, chi, X1, N, h->S1, N));
+    const char* outer = h->tag;
+    const std::string t2 = std::string(outer) + ".X2", t3 = std::string(outer) + ".X3",
+                      t4 = std::string(outer) + ".X4";
+    {
+        ProfTag tg(h, t2.c_str());
+        CKS(gemm(h, false, false, N, N, chi, Tp, chi, X1, N, h->S1, N));
+    }
+    if (h->opt.precision == CTM_OZAKI_BF16 && !open) {
+        // The same contraction with every permutation folded into the operand
+        // views of the tensor-core products and into the output layout.
+        const long long c = chi, Dl = D, dD2 = (long long)d * D2, M3 = c * c * D2;
+        // X3[(a,l',u',b), (s,r,d)] = X2[a,l,l',u,u',b] over (l,u) with Alu[(l,u),(s,r,d)]
+        const OzView x2r{4, {chi, D, D, chi}, {Dl * Dl * Dl * Dl * c, Dl * Dl * c, c, 1}};
+        const OzView x2k{2, {D, D, 1, 1}, {Dl * Dl * Dl * c, Dl * c, 0, 0}};
+        const OzView alu_n{1, {(int)dD2, 1, 1, 1}, {1, 0, 0, 0}}, alu_k{1, {D2, 1, 1, 1}, {dD2, 0, 0, 0}};
+        const OzView x3r{1, {(int)M3, 1, 1, 1}, {dD2, 0, 0, 0}}, x3c{1, {(int)dD2, 1, 1, 1}, {1, 0, 0, 0}};
+        {
+            ProfTag tg(h, t3.c_str());
+            CKS(gemm_v(h, (int)M3, (int)dD2, D2, h->S1, x2r, x2k, Alu, alu_n, alu_k, h->S2, x3r, x3c));
+        }
+        // Q[(a,d,d'), (b,r,r')] = X3[a,l',u',b,s,r,d] over (s,l',u') with A[(s,l',u'),(r',d')]
+        const OzView s2r{4, {chi, chi, D, D}, {Dl * c * dD2 * Dl, dD2, Dl, 1}};
+        const OzView s2k{3, {d, D, D, 1}, {D2, Dl * c * dD2, c * dD2, 0}};
+        const OzView a_n{1, {D2, 1, 1, 1}, {1, 0, 0, 0}}, a_k{1, {(int)dD2, 1, 1, 1}, {D2, 0, 0, 0}};
+        const OzView qr{4, {chi, chi, D, D}, {(long long)D2 * N, D2, Dl, Dl * N}};
+        const OzView qc{2, {D, D, 1, 1}, {1, N, 0, 0}};
+        ProfTag tg(h, t4.c_str());
+        return gemm_v(h, (int)M3, D2, (int)dD2, h->S2, s2r, s2k, A, a_n, a_k, out, qr, qc);
+    }
     // -> [a,l',u',b,l,u]
     CKS(perm(h, h->S1, h->S2, {chi, D, D, D, D, chi}, {0, 2, 4, 5, 1, 3}));
     // X3[(a,l',u',b), (s,r,d)] = X2p[(a,l',u',b), (l,u)] Alu[(l,u), (s,r,d)]
@@ -323,6 +469,7 @@ ctm_status corner_core(ctm_ctx* h, const double* X1, const double* Tp, const dou
 
 // corner c (0..3 = C1..C4 position) of site i as an N x N matrix.
 ctm_status enlarged_corner(ctm_ctx* h, int i, int c, double* out) {
+    ProfTag tg(h, "corner");
     const int chi = h->chi, N = h->N;
     CKS(gemm(h, false, false, chi, N, chi, h->env[i][Cw(c)], chi, h->env[i][Tw(c)], N, h->X1, N));
     return corner_core(h, h->X1, h->env[i][Tw(c + 3)], h->A[i][c & 3], h->Alu[i][c & 3], out, false);
@@ -332,6 +479,7 @@ ctm_status enlarged_corner(ctm_ctx* h, int i, int c, double* out) {
 // randomised SVD of M = H_u^T H_d and the projectors of one cut
 // ----------------------------------------------------------------------------
 ctm_status applyM(ctm_ctx* h, const double* X, double* out, int cols) {
+    ProfTag tg(h, "rsvd.apply");
     const int N = h->N;
     CKS(gemm(h, true, false, N, cols, N, h->E[2], N, X, cols, h->t1, cols));      // E_br^T X
     CKS(gemm(h, true, false, N, cols, N, h->E[3], N, h->t1, cols, h->t2, cols));  // E_bl^T
@@ -340,6 +488,7 @@ ctm_status applyM(ctm_ctx* h, const double* X, double* out, int cols) {
     return CTM_OK;
 }
 ctm_status applyMT(ctm_ctx* h, const double* X, double* out, int cols) {
+    ProfTag tg(h, "rsvd.apply");
     const int N = h->N;
     CKS(gemm(h, false, false, N, cols, N, h->E[1], N, X, cols, h->t1, cols));      // E_ur X
     CKS(gemm(h, false, false, N, cols, N, h->E[0], N, h->t1, cols, h->t2, cols));  // E_ul
@@ -348,12 +497,20 @@ ctm_status applyMT(ctm_ctx* h, const double* X, double* out, int cols) {
     return CTM_OK;
 }
 
-ctm_status projectors(ctm_ctx* h, int slot) {
+// cut: (frame, column, row) index 0..15, keys the warm-start basis
+ctm_status projectors(ctm_ctx* h, int slot, int cut) {
+    ProfTag tg(h, "projector");
     const int N = h->N, k = h->k, chi = h->chi;
-    const int q = (k == N) ? 0 : h->q;
-    CK(ctm::rng_normal(h->Om, (size_t)N * k, h->opt.seed, h->rng_counter++, h->stream));
-    CKS(applyM(h, h->Om, h->Yb, k));
-    CKS(qr_(h, h->Yb, h->Qm, h->Rb));
+    const bool warm_on = h->opt.rsvd_warm_start && k < N;
+    const bool warm = warm_on && h->warm_valid[cut];
+    const int q = (k == N || warm) ? 0 : h->q;
+    const double* Om = h->Om;
+    if (warm) Om = h->warmV[cut];  // one more subspace iteration from last sweep's basis
+    else CK(ctm::rng_normal(h->Om, (size_t)N * k, h->opt.seed, h->rng_counter++, h->stream));
+    CKS(applyM(h, Om, h->Yb, k));
+    const bool chol = warm && k <= 160;  // warm bases: Cholesky QR; cold: Householder
+    if (chol) CKS(qr_chol(h, h->Yb, h->Qm, h->Rb));
+    else CKS(qr_(h, h->Yb, h->Qm, h->Rb));
     for (int it = 0; it < q; ++it) {
         CKS(applyMT(h, h->Qm, h->Zb, k));
         CKS(qr_(h, h->Zb, h->Qm2, h->Rb));
@@ -362,7 +519,13 @@ ctm_status projectors(ctm_ctx* h, int slot) {
     }
     // B^T = M^T Q = Q_b R_b  ->  B = R_b^T Q_b^T ; SVD(R_b^T) = U' S W^T
     CKS(applyMT(h, h->Qm, h->Zb, k));
-    CKS(qr_(h, h->Zb, h->Qb, h->Rb));
+    if (chol) CKS(qr_chol(h, h->Zb, h->Qb, h->Rb));
+    else CKS(qr_(h, h->Zb, h->Qb, h->Rb));
+    if (warm_on) {
+        CK(cudaMemcpyAsync(h->warmV[cut], h->Qb, (size_t)N * k * sizeof(double), cudaMemcpyDeviceToDevice,
+                           h->stream));
+        h->warm_valid[cut] = true;
+    }
     CKS(perm(h, h->Rb, h->G, {k, k}, {1, 0}));
     CKS(svd_(h));
     // U = Q U'[:, :chi], V = Q_b W[:, :chi]
@@ -397,8 +560,9 @@ ctm_status left_move(ctm_ctx* h, int m, int x) {
         CKS(enlarged_corner(h, tr, m + 1, h->E[1]));
         CKS(enlarged_corner(h, br, m + 2, h->E[2]));
         CKS(enlarged_corner(h, bl, m + 3, h->E[3]));
-        CKS(projectors(h, y));
+        CKS(projectors(h, y, ((m & 3) * 2 + x) * 2 + y));
     }
+    ProfTag tg(h, "absorb");
     for (int y = 0; y < 2; ++y) {
         const int i = FM.site(m, x, y), j = FM.site(m, x + 1, y);
         const int ym = (y + 1) % 2;  // cut between rows y-1 and y
@@ -422,9 +586,35 @@ ctm_status left_move(ctm_ctx* h, int m, int x) {
     return CTM_OK;
 }
 
-ctm_status one_sweep(ctm_ctx* h) {
+ctm_status one_sweep_eager(ctm_ctx* h) {
     for (int m = 0; m < 4; ++m)
         for (int x = 0; x < 2; ++x) CKS(left_move(h, m, x));
+    return CTM_OK;
+}
+
+// A sweep's launch sequence is fixed once every cut has a warm basis (or
+// when the range finder never warm-starts): capture it once, replay it.
+ctm_status one_sweep(ctm_ctx* h) {
+    bool steady = !h->opt.rsvd_warm_start || h->k == h->N;
+    if (!steady) {
+        steady = true;
+        for (bool w : h->warm_valid) steady = steady && w;
+    }
+    if (!h->use_graphs || h->prof || !steady) return one_sweep_eager(h);
+    if (!h->graph_exec) {
+        CK(cudaStreamBeginCapture(h->stream, cudaStreamCaptureModeThreadLocal));
+        const ctm_status st = one_sweep_eager(h);
+        cudaGraph_t g = nullptr;
+        const cudaError_t e = cudaStreamEndCapture(h->stream, &g);
+        if (st != CTM_OK) {
+            if (g) cudaGraphDestroy(g);
+            return st;
+        }
+        CK(e);
+        h->graph = g;
+        CK(cudaGraphInstantiate(&h->graph_exec, h->graph, 0));
+    }
+    CK(cudaGraphLaunch(h->graph_exec, h->stream));
     return CTM_OK;
 }
 
@@ -595,6 +785,7 @@ ctm_status ctm_default_options(ctm_options* o) {
     o->sv_cutoff_rel = 1e-12;
     o->seed = 0;
     o->exact_svd_max_n = 256;
+    o->rsvd_warm_start = 1;
     return CTM_OK;
 }
 
@@ -658,6 +849,8 @@ ctm_status ctm_create(int d, int D, const ctm_options* o, void* stream, ctm_hand
     A_(&h->Sv, h->k); A_(&h->inv, h->k);
     const size_t tk = std::max(z.Nk, z.Nchi);
     A_(&h->Uc, z.Nchi); A_(&h->Vc, z.Nchi); A_(&h->t1, tk); A_(&h->t2, tk);
+    A_(&h->cq_G, z.kk); A_(&h->cq_R1, z.kk); A_(&h->cq_R1i, z.kk); A_(&h->cq_R2, z.kk); A_(&h->cq_R2i, z.kk);
+    A_(&h->cq_d, h->k); A_(&h->cq_Q1, z.Nk);
     A_(&h->newC1, z.C); A_(&h->newC4, z.C); A_(&h->newT4, z.T); A_(&h->tmpT, z.T);
     A_(&h->Lh, z.Nchi * d * d); A_(&h->Rh, z.Nchi * d * d);
     A_(&h->rho, std::max<size_t>(64 * 64, (size_t)d * d * d * d));
@@ -670,6 +863,8 @@ ctm_status ctm_create(int d, int D, const ctm_options* o, void* stream, ctm_hand
     if (st == CTM_OK) st = alloc(h, &h->sval_ws, svals_ws_bytes(h->chi, 16));
     if (st == CTM_OK) st = alloc(h, (void**)&h->maxbits, 64 * sizeof(unsigned long long));
     if (st == CTM_OK) st = alloc(h, (void**)&h->flag, 64);
+    if (o->rsvd_warm_start && h->k < h->N)
+        for (int c = 0; c < 16 && st == CTM_OK; ++c) st = allocd(h, &h->warmV[c], z.Nk);
     if (st == CTM_OK && o->precision == CTM_OZAKI_BF16) {
         const OzBounds zb = oz_bounds(d, D, h->chi, h->k, o->ozaki_slices);
         h->ozA_n = zb.a;
@@ -678,6 +873,11 @@ ctm_status ctm_create(int d, int D, const ctm_options* o, void* stream, ctm_hand
         st = alloc(h, &h->ozA, h->ozA_n);
         if (st == CTM_OK) st = alloc(h, &h->ozB, h->ozB_n);
         if (st == CTM_OK) st = alloc(h, &h->ozW, h->ozW_n);
+        for (int c = 0; c < 8 && st == CTM_OK; ++c) {
+            h->ozc[c].ptr = h->E[c / 2];
+            h->ozc[c].trans = (c & 1) != 0;
+            st = alloc(h, &h->ozc[c].buf, ctm::oz_split_bytes(h->N, h->N, o->ozaki_slices));
+        }
     }
     if (st != CTM_OK) {
         g_err = h->err;
@@ -696,6 +896,8 @@ ctm_status ctm_create(int d, int D, const ctm_options* o, void* stream, ctm_hand
 ctm_status ctm_destroy(ctm_handle h) {
     if (!h) return CTM_OK;
     if (h->stream) cudaStreamSynchronize(h->stream);
+    if (h->graph_exec) cudaGraphExecDestroy(h->graph_exec);
+    if (h->graph) cudaGraphDestroy(h->graph);
     for (void* p : h->allocs) cudaFree(p);
     for (cudaEvent_t e : h->ev_pool) cudaEventDestroy(e);
     if (h->own_stream && h->stream) cudaStreamDestroy(h->stream);
@@ -713,6 +915,7 @@ ctm_status ctm_set_tensor(ctm_handle h, int site, const double* A, int on_device
     for (int r = 0; r < 4; ++r) CKS(perm(h, h->A[site][r], h->Alu[site][r], {d, D, D, D, D}, {1, 2, 0, 3, 4}));
     CK(cudaStreamSynchronize(h->stream));
     h->have_A[site] = true;
+    for (bool& w : h->warm_valid) w = false;
     return CTM_OK;
 }
 
@@ -723,6 +926,7 @@ ctm_status ctm_set_env(ctm_handle h, int site, int which, const double* t, int o
                        on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice, h->stream));
     CK(cudaStreamSynchronize(h->stream));
     h->env_set |= 1u << (site * 8 + which);
+    for (bool& w : h->warm_valid) w = false;
     return CTM_OK;
 }
 
@@ -938,16 +1142,37 @@ ctm_status ctm_profile_enable(ctm_handle h, int on) {
 ctm_status ctm_profile_read(ctm_handle h, ctm_profile_data* out, int reset) {
     if (!h || !out) return CTM_ERR_ARG;
     prof_collect(h);
-    for (int c = 0; c < 4; ++c) {
+    for (int c = 0; c < 8; ++c) {
         out->ms[c] = h->p_ms[c];
         out->flops[c] = h->p_flops[c];
         out->bytes[c] = h->p_bytes[c];
         out->calls[c] = h->p_calls[c];
         if (reset) h->p_ms[c] = h->p_flops[c] = h->p_bytes[c] = 0, h->p_calls[c] = 0;
     }
+    if (reset) h->tags.clear();
     return CTM_OK;
 }
 
 long long ctm_kernel_launches(void) { return ctm::g_launches; }
+
+ctm_status ctm_profile_report(ctm_handle h, char* buf, size_t len, int reset) {
+    if (!h || !buf || len == 0) return CTM_ERR_ARG;
+    prof_collect(h);
+    std::string out = "{";
+    bool first = true;
+    char tmp[256];
+    for (const auto& kv : h->tags) {
+        snprintf(tmp, sizeof(tmp), "%s\"%s\": {\"ms\": %.4f, \"calls\": %lld, \"flops\": %.6g, \"bytes\": %.6g}",
+                 first ? "" : ", ", kv.first.c_str(), kv.second.ms, kv.second.calls, kv.second.flops,
+                 kv.second.bytes);
+        out += tmp;
+        first = false;
+    }
+    out += "}";
+    if (reset) h->tags.clear();
+    if (out.size() + 1 > len) return CTM_ERR_ARG;
+    memcpy(buf, out.c_str(), out.size() + 1);
+    return CTM_OK;
+}
 
 }  // extern "C"

@@ -41,6 +41,12 @@ cudaError_t dot(const double* x, const double* y, size_t n, double* result, cuda
 // ---- dense linear algebra (linalg.cu) ---------------------------------------
 size_t qr_ws_bytes(int N, int k);
 cudaError_t qr(const double* Y, int N, int k, double* Q, double* R, void* ws, cudaStream_t s);
+// G + shift_rel*mean(diag) I = R^T R; R upper, Rinv = R^{-1} (k <= 160, k x k row-major)
+cudaError_t chol_inv(const double* G, int k, double shift_rel, double* R, double* Rinv, cudaStream_t s);
+// d_i = sqrt(G_ii); G <- D^-1 G D^-1 (k <= 1024)
+cudaError_t equilibrate(double* G, int k, double* d, cudaStream_t s);
+// scale rows (or columns) of a k x k matrix by w (or divide by it)
+cudaError_t scale_rc(double* X, int k, const double* w, bool rows, bool inv, cudaStream_t s);
 size_t svd_ws_bytes(int k);
 cudaError_t svd(const double* G, int k, double* U, double* S, double* V, void* ws, cudaStream_t s);
 // svd() with its workspace in a static device array (k <= svd_noalloc_max_k())
@@ -52,13 +58,26 @@ size_t svals_ws_bytes(int k, int nb);
 cudaError_t svals_normalised(const double* Gs, int k, int nb, double* out, void* ws, cudaStream_t s);
 
 // ---- emulated-FP64 GEMM on the tensor cores (ozaki.cu) ----------------------
+// strided multi-index view (row-major over dim[0..n-1])
+struct OzView {
+    int n;
+    int dim[4];
+    long long stride[4];
+};
 // Split an R x K FP64 operand (element (r,k) at X[r*rs + k*cs]) into s BF16
 // slices [s][R][K8] plus per-row exponents, in a buffer of oz_split_bytes.
 size_t oz_split_bytes(int R, int K, int s);
 cudaError_t oz_split(const double* X, int R, int K, long long rs, long long cs, int s, void* buf, cudaStream_t st);
+// element (r, k) at X[view(rv, r) + view(kv, k)]
+cudaError_t oz_split_view(const double* X, int R, int K, const OzView& rv, const OzView& kv, int s, void* buf,
+                          cudaStream_t st);
 // C[M,N] = alpha A B + beta C from split A (M rows) and split B (N rows = columns of B).
 size_t oz_gemm_ws_bytes(int M, int N, int K, int s);
 cudaError_t oz_gemm(int M, int N, int K, int s, const void* Asplit, const void* Bsplit, double alpha, double beta,
                     double* C, int ldc, void* ws, size_t ws_bytes, int* err, cudaStream_t st);
+// C written at C[view(out_r, m) + view(out_c, n)]
+cudaError_t oz_gemm_view(int M, int N, int K, int s, const void* Asplit, const void* Bsplit, double alpha,
+                         double beta, double* C, const OzView& out_r, const OzView& out_c, void* ws, size_t ws_bytes,
+                         int* err, cudaStream_t st);
 
 }  // namespace ctm

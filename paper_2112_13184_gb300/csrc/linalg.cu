@@ -27,92 +27,6 @@ __device__ __forceinline__ double block_sum(double v, double* sm) {
     return t;
 }
 
-__device__ __forceinline__ double block_max(double v, double* sm) {
-    for (int o = 16; o > 0; o >>= 1) v = fmax(v, __shfl_xor_sync(0xffffffffu, v, o));
-    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
-    __syncthreads();
-    if (lane == 0) sm[w] = v;
-    __syncthreads();
-    double t = 0.0;
-    const int nw = (blockDim.x + 31) >> 5;
-    for (int i = 0; i < nw; ++i) t = fmax(t, sm[i]);
-    return t;
-}
-
-// Reflector of x = At[j][j:N] in the normalised form H = I - tau v v^T,
-// v_j = 1, v_i = x_i / (x_j - beta), beta = -sign(x_j) |x|, tau in [1, 2]
-// (the form of LAPACK's xLARFG): no quantity overflows when |x| is tiny.
-// The norm is taken of x / max|x_i| so that squares do not underflow.
-struct Reflector {
-    double beta, tau, inv_denom;
-};
-__device__ Reflector make_reflector(const double* x, int j, int N, double* sm) {
-    double mx = 0.0;
-    for (int i = j + threadIdx.x; i < N; i += blockDim.x) mx = fmax(mx, fabs(x[i]));
-    mx = block_max(mx, sm);
-    Reflector r{x[j], 0.0, 0.0};
-    if (mx == 0.0) return r;  // H = I
-    const double inv = 1.0 / mx;
-    double s2 = 0.0;
-    for (int i = j + threadIdx.x; i < N; i += blockDim.x) {
-        const double t = x[i] * inv;
-        s2 = fma(t, t, s2);
-    }
-    s2 = block_sum(s2, sm);
-    const double sig = mx * sqrt(s2);
-    const double x0 = x[j];
-    r.beta = (x0 >= 0.0) ? -sig : sig;
-    const double denom = x0 - r.beta;  // |denom| = |x0| + sig >= sig > 0
-    r.tau = (r.beta - x0) / r.beta;
-    r.inv_denom = 1.0 / denom;
-    return r;
-}
-
-// One Householder step j on At (k rows of length N, row c = column c).
-// CTA b works on column c = j + b.  Every CTA recomputes the reflector of
-// column j from At[j] (read-only in this launch); CTA 0 stores it.
-__global__ void __launch_bounds__(QR_THREADS) k_house_step(double* __restrict__ At, double* __restrict__ V,
-                                                           double* __restrict__ tau, double* __restrict__ beta,
-                                                           double* __restrict__ R, int N, int k, int j) {
-    __shared__ double sm[32];
-    const int c = j + blockIdx.x;
-    const double* x = At + (size_t)j * N;
-    const Reflector rf = make_reflector(x, j, N, sm);
-    if (blockIdx.x == 0) {
-        double* v = V + (size_t)j * N;
-        for (int i = threadIdx.x; i < N; i += blockDim.x)
-            v[i] = (i < j) ? 0.0 : (i == j ? 1.0 : x[i] * rf.inv_denom);
-        if (threadIdx.x == 0) { tau[j] = rf.tau; beta[j] = rf.beta; }
-        return;
-    }
-    if (rf.tau == 0.0) {
-        if (threadIdx.x == 0) R[(size_t)j * k + c] = At[(size_t)c * N + j];
-        return;
-    }
-    double* a = At + (size_t)c * N;
-    double w = 0.0;
-    for (int i = j + threadIdx.x; i < N; i += blockDim.x) w = fma(i == j ? 1.0 : x[i] * rf.inv_denom, a[i], w);
-    w = block_sum(w, sm) * rf.tau;
-    for (int i = j + threadIdx.x; i < N; i += blockDim.x) a[i] -= w * (i == j ? 1.0 : x[i] * rf.inv_denom);
-    // thread 0 owns index j in the strided loop, so it reads its own update
-    if (threadIdx.x == 0) R[(size_t)j * k + c] = a[j];
-}
-
-// Q accumulation step j: Qt rows c >= j  <-  (I - tau v v^T) Qt[c].
-__global__ void __launch_bounds__(QR_THREADS) k_house_apply(double* __restrict__ Qt, const double* __restrict__ V,
-                                                            const double* __restrict__ tau, int N, int j) {
-    __shared__ double sm[32];
-    const double t = tau[j];
-    if (t == 0.0) return;
-    const int c = j + blockIdx.x;
-    const double* v = V + (size_t)j * N;
-    double* q = Qt + (size_t)c * N;
-    double w = 0.0;
-    for (int i = j + threadIdx.x; i < N; i += blockDim.x) w = fma(v[i], q[i], w);
-    w = block_sum(w, sm) * t;
-    for (int i = j + threadIdx.x; i < N; i += blockDim.x) q[i] -= w * v[i];
-}
-
 __global__ void k_eye_rows(double* __restrict__ Qt, int N, int k) {
     const size_t total = (size_t)k * N;
     for (size_t t = blockIdx.x * (size_t)blockDim.x + threadIdx.x; t < total; t += (size_t)gridDim.x * blockDim.x) {
@@ -139,6 +53,265 @@ __global__ void k_qr_out(const double* __restrict__ Qt, const double* __restrict
         if (c == j) v = fabs(alpha[j]);
         else if (c > j) v = sg * Rtmp[t];
         R[t] = v;
+    }
+}
+
+// ---------------------------------------------------------------------------
+// Householder QR, two launches per step over (row chunk x column) tiles so
+// that every step uses the whole GPU.  Step j, phase A: every tile forms the
+// partial dot x.a_c of the current column x = At[j] with a column a_c = At[c]
+// (c = j gives |x|^2) over its rows.  Phase B: every tile reduces the
+// partials in fixed order and applies the reflector in normalised form
+// H = I - tau v v^T, v_j = 1, v_i = x_i / (x_j - beta), beta = -sign(x_j)|x|,
+// tau = (beta - x_j)/beta in [1, 2], using v.a_c = (x.a_c - beta a_c[j]) /
+// (x_j - beta).  a_c[j] is recorded in phase A, before phase B changes it.
+// ---------------------------------------------------------------------------
+constexpr int QR_CHUNK = 512;
+constexpr int QR2_THREADS = 128;
+
+__global__ void __launch_bounds__(QR2_THREADS) k_qr_dots(const double* __restrict__ At, int N, int k, int j,
+                                                         double* __restrict__ P, double* __restrict__ Aj) {
+    __shared__ double sm[32];
+    const int ch = blockIdx.x, c = j + blockIdx.y;
+    const int i0 = max(j, ch * QR_CHUNK), i1 = min(N, (ch + 1) * QR_CHUNK);
+    const double* x = At + (size_t)j * N;
+    const double* a = At + (size_t)c * N;
+    double p = 0.0;
+    for (int i = i0 + threadIdx.x; i < i1; i += blockDim.x) p = fma(x[i], a[i], p);
+    p = block_sum(p, sm);
+    if (threadIdx.x == 0) {
+        P[(size_t)ch * k + c] = p;
+        if (j >= ch * QR_CHUNK && j < (ch + 1) * QR_CHUNK) Aj[c] = a[j];
+    }
+}
+
+__global__ void __launch_bounds__(QR2_THREADS) k_qr_update(double* __restrict__ At, double* __restrict__ V,
+                                                           double* __restrict__ tau, double* __restrict__ beta,
+                                                           double* __restrict__ R, int N, int k, int j, int nch,
+                                                           const double* __restrict__ P,
+                                                           const double* __restrict__ Aj) {
+    const int ch = blockIdx.x, c = j + blockIdx.y;
+    const int i0 = max(j, ch * QR_CHUNK), i1 = min(N, (ch + 1) * QR_CHUNK);
+    const bool owns_j = j >= ch * QR_CHUNK && j < (ch + 1) * QR_CHUNK;
+    double s2 = 0.0, xa = 0.0;
+    for (int q = 0; q < nch; ++q) {
+        s2 += P[(size_t)q * k + j];
+        xa += P[(size_t)q * k + c];
+    }
+    const double xj = Aj[j];
+    const double* x = At + (size_t)j * N;
+    if (s2 == 0.0) {  // zero column: H = I
+        if (c == j) {
+            if (owns_j && threadIdx.x == 0) {
+                V[(size_t)j * N + j] = 1.0;
+                tau[j] = 0.0;
+                beta[j] = xj;
+            }
+        } else if (owns_j && threadIdx.x == 0) {
+            R[(size_t)j * k + c] = Aj[c];
+        }
+        return;
+    }
+    const double sig = sqrt(s2);
+    const double bt = xj >= 0.0 ? -sig : sig;
+    const double inv = 1.0 / (xj - bt);  // |xj - bt| = |xj| + sig >= sig > 0
+    const double tu = (bt - xj) / bt;
+    if (c == j) {
+        double* v = V + (size_t)j * N;
+        for (int i = i0 + threadIdx.x; i < i1; i += blockDim.x) v[i] = (i == j) ? 1.0 : x[i] * inv;
+        if (owns_j && threadIdx.x == 0) {
+            tau[j] = tu;
+            beta[j] = bt;
+        }
+        return;
+    }
+    const double w = tu * (xa - bt * Aj[c]) * inv;
+    double* a = At + (size_t)c * N;
+    for (int i = i0 + threadIdx.x; i < i1; i += blockDim.x) a[i] -= w * ((i == j) ? 1.0 : x[i] * inv);
+    if (owns_j && threadIdx.x == 0) R[(size_t)j * k + c] = Aj[c] - w;
+}
+
+// Q accumulation step j: Qt rows c >= j  <-  (I - tau v v^T) Qt[c]
+__global__ void __launch_bounds__(QR2_THREADS) k_qt_dots(const double* __restrict__ Qt, const double* __restrict__ V,
+                                                         const double* __restrict__ tau, int N, int k, int j,
+                                                         double* __restrict__ P) {
+    __shared__ double sm[32];
+    if (tau[j] == 0.0) return;
+    const int ch = blockIdx.x, c = j + blockIdx.y;
+    const int i0 = max(j, ch * QR_CHUNK), i1 = min(N, (ch + 1) * QR_CHUNK);
+    const double* v = V + (size_t)j * N;
+    const double* q = Qt + (size_t)c * N;
+    double p = 0.0;
+    for (int i = i0 + threadIdx.x; i < i1; i += blockDim.x) p = fma(v[i], q[i], p);
+    p = block_sum(p, sm);
+    if (threadIdx.x == 0) P[(size_t)ch * k + c] = p;
+}
+
+__global__ void __launch_bounds__(QR2_THREADS) k_qt_update(double* __restrict__ Qt, const double* __restrict__ V,
+                                                           const double* __restrict__ tau, int N, int k, int j,
+                                                           int nch, const double* __restrict__ P) {
+    const double tu = tau[j];
+    if (tu == 0.0) return;
+    const int ch = blockIdx.x, c = j + blockIdx.y;
+    const int i0 = max(j, ch * QR_CHUNK), i1 = min(N, (ch + 1) * QR_CHUNK);
+    double d = 0.0;
+    for (int q = 0; q < nch; ++q) d += P[(size_t)q * k + c];
+    const double w = tu * d;
+    const double* v = V + (size_t)j * N;
+    double* qc = Qt + (size_t)c * N;
+    for (int i = i0 + threadIdx.x; i < i1; i += blockDim.x) qc[i] -= w * v[i];
+}
+
+// ---------------------------------------------------------------------------
+// One-sided Jacobi in a single launch: one thread-block cluster per matrix,
+// its warps share the round's pairs; columns live in global memory and are
+// read and written through L2 (ld.cg / st.cg); a cluster barrier (release /
+// acquire) separates rounds.  Every thread runs every barrier, so the
+// cluster cannot wait on a thread that left.
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ void cluster_sync() {
+    asm volatile("barrier.cluster.arrive.release.aligned;\n\tbarrier.cluster.wait.acquire.aligned;" ::: "memory");
+}
+
+__global__ void __launch_bounds__(256) k_jacobi_cluster(double* __restrict__ Gt, double* __restrict__ Wt, int k,
+                                                       int n, int max_sweeps, double tol,
+                                                       unsigned long long* __restrict__ off, int csize) {
+    const int b = blockIdx.x / csize, rank = blockIdx.x % csize;
+    const int warps = blockDim.x >> 5, lane = threadIdx.x & 31;
+    const int gw = rank * warps + (threadIdx.x >> 5), nw = csize * warps;
+    double* g = Gt + (size_t)b * k * k;
+    double* wm = Wt ? Wt + (size_t)b * k * k : nullptr;
+    unsigned long long* offb = off + (size_t)b * max_sweeps;
+    for (int sw = 0; sw < max_sweeps; ++sw) {
+        for (int r = 0; r < n - 1; ++r) {
+            for (int p = gw; p < n / 2; p += nw) {
+                auto pos = [&](int i) { return i == 0 ? 0 : 1 + (i - 1 + r) % (n - 1); };
+                int P = pos(p), Q = pos(n - 1 - p);
+                if (P >= k || Q >= k) continue;
+                if (P > Q) { const int t = P; P = Q; Q = t; }
+                double* gp = g + (size_t)P * k;
+                double* gq = g + (size_t)Q * k;
+                double a = 0.0, bb = 0.0, c = 0.0;
+                for (int i = lane; i < k; i += 32) {
+                    const double x = __ldcg(gp + i), y = __ldcg(gq + i);
+                    a = fma(x, x, a);
+                    bb = fma(y, y, bb);
+                    c = fma(x, y, c);
+                }
+                for (int o = 16; o > 0; o >>= 1) {
+                    a += __shfl_xor_sync(0xffffffffu, a, o);
+                    bb += __shfl_xor_sync(0xffffffffu, bb, o);
+                    c += __shfl_xor_sync(0xffffffffu, c, o);
+                }
+                if (a == 0.0 || bb == 0.0) continue;
+                const double rel = fabs(c) / (sqrt(a) * sqrt(bb));
+                if (lane == 0) atomicMax(offb + sw, (unsigned long long)__double_as_longlong(rel));
+                if (!(rel > tol)) continue;
+                const double z = (bb - a) / (2.0 * c);
+                const double t = (z >= 0.0 ? 1.0 : -1.0) / (fabs(z) + sqrt(1.0 + z * z));
+                const double cs = 1.0 / sqrt(1.0 + t * t), sn = cs * t;
+                for (int i = lane; i < k; i += 32) {
+                    const double x = __ldcg(gp + i), y = __ldcg(gq + i);
+                    __stcg(gp + i, cs * x - sn * y);
+                    __stcg(gq + i, sn * x + cs * y);
+                }
+                if (wm) {
+                    double* wp = wm + (size_t)P * k;
+                    double* wq = wm + (size_t)Q * k;
+                    for (int i = lane; i < k; i += 32) {
+                        const double x = __ldcg(wp + i), y = __ldcg(wq + i);
+                        __stcg(wp + i, cs * x - sn * y);
+                        __stcg(wq + i, sn * x + cs * y);
+                    }
+                }
+            }
+            cluster_sync();
+        }
+        const double o = __longlong_as_double((long long)__ldcg(offb + sw));
+        cluster_sync();  // everyone has read this sweep's value before anyone moves on
+        if (o < tol) break;
+    }
+}
+
+// ---------------------------------------------------------------------------
+// Cholesky factor and its inverse of a small SPD matrix (one CTA, k <= 160,
+// the matrix in shared memory).  G + shift I = R^T R with R upper triangular
+// and positive diagonal; pivots below 1e-30 of the mean diagonal are clamped.
+// Lower triangle of S holds L = R^T (diagonal kept apart), the upper triangle
+// receives L^{-1} transposed = R^{-1}, column by column (one warp each).
+// ---------------------------------------------------------------------------
+__global__ void __launch_bounds__(1024) k_chol_inv(const double* __restrict__ G, int k, double shift_rel,
+                                                  double* __restrict__ R, double* __restrict__ Rinv) {
+    extern __shared__ double S[];  // k*k + k
+    double* dg = S + (size_t)k * k;
+    __shared__ double sm[32];
+    const int tid = threadIdx.x, nt = blockDim.x;
+    double tr = 0.0;
+    for (int i = tid; i < k * k; i += nt) {
+        S[i] = G[i];
+        if (i / k == i % k) tr += G[i];
+    }
+    tr = block_sum(tr, sm);
+    const double mean = tr > 0.0 ? tr / k : 1.0;
+    for (int i = tid; i < k; i += nt) S[(size_t)i * k + i] += shift_rel * mean;
+    __syncthreads();
+    for (int j = 0; j < k; ++j) {
+        double piv = S[(size_t)j * k + j];
+        if (!(piv > 1e-30 * mean)) piv = 1e-30 * mean;
+        const double d = sqrt(piv);
+        const double inv = 1.0 / d;
+        for (int i = j + 1 + tid; i < k; i += nt) S[(size_t)i * k + j] *= inv;
+        if (tid == 0) dg[j] = d;
+        __syncthreads();
+        const int m = k - j - 1;  // trailing lower triangle, m(m+1)/2 entries
+        for (int t = tid; t < m * (m + 1) / 2; t += nt) {
+            int i = (int)((sqrtf(8.0f * (float)t + 1.0f) - 1.0f) * 0.5f);  // row estimate, corrected below
+            while ((i + 1) * (i + 2) / 2 <= t) ++i;
+            while (i * (i + 1) / 2 > t) --i;
+            const int l = t - i * (i + 1) / 2;
+            const int ii = j + 1 + i, ll = j + 1 + l;
+            S[(size_t)ii * k + ll] -= S[(size_t)ii * k + j] * S[(size_t)ll * k + j];
+        }
+        __syncthreads();
+    }
+    // L^{-1}: column c by forward substitution; X[i][c] stored at S[c][i] (i >= c)
+    const int warp = tid >> 5, lane = tid & 31, nw = nt >> 5;
+    for (int c = warp; c < k; c += nw) {
+        if (lane == 0) S[(size_t)c * k + c] = 1.0 / dg[c];
+        __syncwarp();
+        for (int i = c + 1; i < k; ++i) {
+            double acc = 0.0;
+            for (int m = c + lane; m < i; m += 32) acc = fma(S[(size_t)i * k + m], S[(size_t)c * k + m], acc);
+            for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
+            if (lane == 0) S[(size_t)c * k + i] = -acc / dg[i];
+            __syncwarp();
+        }
+    }
+    __syncthreads();
+    for (int t = tid; t < k * k; t += nt) {
+        const int i = t / k, j = t % k;
+        R[t] = j > i ? S[(size_t)j * k + i] : (j == i ? dg[i] : 0.0);  // R = L^T
+        Rinv[t] = j >= i ? S[t] : 0.0;                                 // R^{-1} = (L^{-1})^T
+    }
+}
+
+// d_i = sqrt(G_ii) (1 if 0); G <- D^-1 G D^-1
+__global__ void k_equilibrate(double* __restrict__ G, int k, double* __restrict__ d) {
+    __shared__ double dd[1024];
+    for (int i = threadIdx.x; i < k; i += blockDim.x) {
+        const double v = G[(size_t)i * k + i];
+        dd[i] = v > 0.0 ? sqrt(v) : 1.0;
+        d[i] = dd[i];
+    }
+    __syncthreads();
+    for (int t = threadIdx.x; t < k * k; t += blockDim.x) G[t] /= dd[t / k] * dd[t % k];
+}
+
+// X[i][j] *= (rows ? w[i] : w[j]) ; with inv, divide instead
+__global__ void k_scale_rc(double* __restrict__ X, int k, const double* __restrict__ w, int rows, int inv) {
+    for (int t = blockIdx.x * blockDim.x + threadIdx.x; t < k * k; t += gridDim.x * blockDim.x) {
+        const double f = w[rows ? t / k : t % k];
+        X[t] = inv ? X[t] / f : X[t] * f;
     }
 }
 
@@ -273,32 +446,85 @@ constexpr double JACOBI_TOL = 1e-15;
 
 // ---------------------------------------------------------------------------
 size_t qr_ws_bytes(int N, int k) {
-    return sizeof(double) * (3 * (size_t)k * N + (size_t)k * k + 2 * (size_t)k) + 256;
+    const size_t nch = (size_t)(N + QR_CHUNK - 1) / QR_CHUNK;
+    return sizeof(double) * (3 * (size_t)k * N + (size_t)k * k + 3 * (size_t)k + nch * k) + 256;
 }
 
 cudaError_t qr(const double* Y, int N, int k, double* Q, double* R, void* ws, cudaStream_t s) {
     if (N < k || k <= 0) return cudaErrorInvalidValue;
+    const int nch = (N + QR_CHUNK - 1) / QR_CHUNK;
     double* At = (double*)ws;
     double* V = At + (size_t)k * N;
     double* Qt = V + (size_t)k * N;
     double* Rtmp = Qt + (size_t)k * N;
     double* tau = Rtmp + (size_t)k * k;
-    double* alpha = tau + k;  // diagonal of R before the sign fix
+    double* beta = tau + k;  // diagonal of R before the sign fix
+    double* Aj = beta + k;
+    double* P = Aj + k;
     const int dims[2] = {N, k}, perm[2] = {1, 0};
     cudaError_t e = permute(Y, At, 2, dims, perm, s);
     if (e) return e;
+    e = cudaMemsetAsync(V, 0, sizeof(double) * (size_t)k * N, s);
+    if (e) return e;
     for (int j = 0; j < k; ++j) {
+        const dim3 grid(nch, k - j);
         ++g_launches;
-        k_house_step<<<k - j, QR_THREADS, 0, s>>>(At, V, tau, alpha, Rtmp, N, k, j);
+        k_qr_dots<<<grid, QR2_THREADS, 0, s>>>(At, N, k, j, P, Aj);
+        ++g_launches;
+        k_qr_update<<<grid, QR2_THREADS, 0, s>>>(At, V, tau, beta, Rtmp, N, k, j, nch, P, Aj);
     }
     ++g_launches;
     k_eye_rows<<<grid_for((size_t)k * N), 256, 0, s>>>(Qt, N, k);
     for (int j = k - 1; j >= 0; --j) {
+        const dim3 grid(nch, k - j);
         ++g_launches;
-        k_house_apply<<<k - j, QR_THREADS, 0, s>>>(Qt, V, tau, N, j);
+        k_qt_dots<<<grid, QR2_THREADS, 0, s>>>(Qt, V, tau, N, k, j, P);
+        ++g_launches;
+        k_qt_update<<<grid, QR2_THREADS, 0, s>>>(Qt, V, tau, N, k, j, nch, P);
     }
     ++g_launches;
-    k_qr_out<<<grid_for((size_t)N * k), 256, 0, s>>>(Qt, alpha, Rtmp, Q, R, N, k);
+    k_qr_out<<<grid_for((size_t)N * k), 256, 0, s>>>(Qt, beta, Rtmp, Q, R, N, k);
+    return cudaGetLastError();
+}
+
+// Jacobi on nb matrices: one 16-CTA cluster per matrix when the device
+// allows it (8 otherwise), else one launch per round.
+cudaError_t jacobi(double* Gt, double* Wt, int k, int n, int nb, unsigned long long* off, cudaStream_t s) {
+    static int csize = -1;
+    if (csize < 0) {
+        csize = 0;
+        if (cudaFuncSetAttribute(k_jacobi_cluster, cudaFuncAttributeNonPortableClusterSizeAllowed, 1) == cudaSuccess)
+            csize = 16;
+        else
+            csize = 8;
+        cudaGetLastError();
+    }
+    for (int attempt = 0; attempt < 2 && csize > 0; ++attempt) {
+        cudaLaunchConfig_t cfg = {};
+        cfg.gridDim = dim3((unsigned)(nb * csize), 1, 1);
+        cfg.blockDim = dim3(256, 1, 1);
+        cfg.dynamicSmemBytes = 0;
+        cfg.stream = s;
+        cudaLaunchAttribute at[1];
+        at[0].id = cudaLaunchAttributeClusterDimension;
+        at[0].val.clusterDim.x = csize;
+        at[0].val.clusterDim.y = 1;
+        at[0].val.clusterDim.z = 1;
+        cfg.attrs = at;
+        cfg.numAttrs = 1;
+        ++g_launches;
+        const cudaError_t e = cudaLaunchKernelEx(&cfg, k_jacobi_cluster, Gt, Wt, k, n, JACOBI_MAX_SWEEPS,
+                                                 JACOBI_TOL, off, csize);
+        if (e == cudaSuccess) return cudaSuccess;
+        cudaGetLastError();
+        --g_launches;
+        csize = csize > 8 ? 8 : 0;  // retry with a portable cluster, then give up on clusters
+    }
+    for (int sw = 0; sw < JACOBI_MAX_SWEEPS; ++sw)
+        for (int r = 0; r < n - 1; ++r) {
+            ++g_launches;
+            k_jacobi_round<<<dim3(n / 2, nb), 32, 0, s>>>(Gt, Wt, k, n, r, sw, off, JACOBI_TOL);
+        }
     return cudaGetLastError();
 }
 
@@ -318,11 +544,8 @@ cudaError_t svd(const double* G, int k, double* U, double* S, double* V, void* w
     ++g_launches;
     k_eye_batch<<<grid_for((size_t)k * k), 256, 0, s>>>(Wt, k, 1);
     const int n = k + (k & 1);
-    for (int sw = 0; sw < JACOBI_MAX_SWEEPS; ++sw)
-        for (int r = 0; r < n - 1; ++r) {
-            ++g_launches;
-            k_jacobi_round<<<dim3(n / 2, 1), 32, 0, s>>>(Gt, Wt, k, n, r, sw, off, JACOBI_TOL);
-        }
+    e = jacobi(Gt, Wt, k, n, 1, off, s);
+    if (e) return e;
     ++g_launches;
     k_jacobi_finish<<<1, 256, sizeof(double) * k, s>>>(Gt, Wt, k, U, S, V);
     return cudaGetLastError();
@@ -341,11 +564,8 @@ cudaError_t svals_normalised(const double* Gs, int k, int nb, double* out, void*
     ++g_launches;
     k_transpose_batch<<<grid_for((size_t)nb * k * k), 256, 0, s>>>(Gs, Gt, k, nb);
     const int n = k + (k & 1);
-    for (int sw = 0; sw < JACOBI_MAX_SWEEPS; ++sw)
-        for (int r = 0; r < n - 1; ++r) {
-            ++g_launches;
-            k_jacobi_round<<<dim3(n / 2, nb), 32, 0, s>>>(Gt, nullptr, k, n, r, sw, off, JACOBI_TOL);
-        }
+    e = jacobi(Gt, nullptr, k, n, nb, off, s);
+    if (e) return e;
     ++g_launches;
     k_svals_finish<<<nb, 256, sizeof(double) * k, s>>>(Gt, k, out);
     return cudaGetLastError();
@@ -393,6 +613,34 @@ cudaError_t svd_noalloc(const double* G, int k, double* U, double* S, double* V,
         ws = g_scratch_ptr[dev];
     }
     return svd(G, k, U, S, V, ws, s);
+}
+
+cudaError_t chol_inv(const double* G, int k, double shift_rel, double* R, double* Rinv, cudaStream_t s) {
+    if (k <= 0 || k > 160) return cudaErrorInvalidValue;
+    const size_t smem = sizeof(double) * ((size_t)k * k + k);
+    static bool attr = false;
+    if (!attr) {
+        cudaError_t e = cudaFuncSetAttribute(k_chol_inv, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                             (int)(sizeof(double) * (160 * 160 + 160)));
+        if (e) return e;
+        attr = true;
+    }
+    ++g_launches;
+    k_chol_inv<<<1, 1024, smem, s>>>(G, k, shift_rel, R, Rinv);
+    return cudaGetLastError();
+}
+
+cudaError_t equilibrate(double* G, int k, double* d, cudaStream_t s) {
+    if (k <= 0 || k > 1024) return cudaErrorInvalidValue;
+    ++g_launches;
+    k_equilibrate<<<1, 1024, 0, s>>>(G, k, d);
+    return cudaGetLastError();
+}
+
+cudaError_t scale_rc(double* X, int k, const double* w, bool rows, bool inv, cudaStream_t s) {
+    ++g_launches;
+    k_scale_rc<<<grid_for((size_t)k * k), 256, 0, s>>>(X, k, w, rows ? 1 : 0, inv ? 1 : 0);
+    return cudaGetLastError();
 }
 
 }  // namespace ctm

@@ -37,6 +37,134 @@ constexpr int EPI_WARPS = 12;    // 3 warps per TMEM lane quarter
 constexpr int THREADS = (EPI_WARPS + 2) * 32;  // + producer warp + MMA warp
 constexpr int MAX_S = 6;
 
+// A strided multi-index view: index i = (i_0, ..., i_{n-1}) in row-major
+// order over dims, offset = sum_a i_a * stride[a].  Used to read operands as
+// permuted views of larger tensors and to write results into permuted
+// layouts, so that no FP64 permutation pass is needed.
+struct View {
+    int n;
+    int dim[4];
+    long long stride[4];
+};
+__host__ __device__ __forceinline__ long long view_offset(const View& v, long long i) {
+    long long off = 0;
+#pragma unroll
+    for (int a = 3; a >= 0; --a) {
+        if (a < v.n) {
+            const long long q = i / v.dim[a];
+            off += (i - q * v.dim[a]) * v.stride[a];
+            i = q;
+        }
+    }
+    return off;
+}
+
+// 32-bit decomposition (all view extents here are below 2^31)
+__device__ __forceinline__ long long view_offset32(const View& v, unsigned i) {
+    long long off = 0;
+#pragma unroll
+    for (int a = 3; a >= 0; --a) {
+        if (a < v.n) {
+            const unsigned dm = (unsigned)v.dim[a];
+            const unsigned q = i / dm;
+            off += (long long)(i - q * dm) * v.stride[a];
+            i = q;
+        }
+    }
+    return off;
+}
+
+// walks a view's indices in order, one add per step (carry on wrap)
+struct Odometer {
+    int idx[4];
+    long long off;
+    __device__ __forceinline__ void init(const View& v, unsigned i) {
+        off = 0;
+#pragma unroll
+        for (int a = 3; a >= 0; --a) {
+            idx[a] = 0;
+            if (a < v.n) {
+                const unsigned dm = (unsigned)v.dim[a];
+                const unsigned q = i / dm;
+                idx[a] = (int)(i - q * dm);
+                off += (long long)idx[a] * v.stride[a];
+                i = q;
+            }
+        }
+    }
+    __device__ __forceinline__ void step(const View& v) {
+#pragma unroll
+        for (int a = 3; a >= 0; --a) {
+            if (a < v.n) {
+                off += v.stride[a];
+                if (++idx[a] < v.dim[a]) return;
+                off -= (long long)v.dim[a] * v.stride[a];
+                idx[a] = 0;
+            }
+        }
+    }
+};
+
+// v * 2^k for finite v, through the exponent field when the result stays
+// normal (the common case), else by ldexp
+__device__ __forceinline__ double scale_pow2(double v, int k) {
+    const long long b = __double_as_longlong(v);
+    const int e = (int)((b >> 52) & 0x7ff);
+    if (v == 0.0) return v;
+    if (e > 0 && e + k > 0 && e + k < 2047) return __longlong_as_double(b + ((long long)k << 52));
+    return ldexp(v, k);
+}
+
+// Z * 2^E as an FP64 number (round to nearest even) with integer operations
+// only: GB300's FP64 pipe is too slow to spend on every output element.
+__device__ __forceinline__ double i64_ldexp(long long Z, int E) {
+    if (Z == 0) return 0.0;
+    const unsigned long long neg = Z < 0 ? 1ull : 0ull;
+    unsigned long long m = neg ? (0ull - (unsigned long long)Z) : (unsigned long long)Z;
+    int sh = (64 - __clzll((long long)m)) - 53;  // bits beyond a 53-bit mantissa
+    unsigned long long mant;
+    if (sh > 0) {
+        const unsigned long long rem = m & ((1ull << sh) - 1), half = 1ull << (sh - 1);
+        mant = m >> sh;
+        if (rem > half || (rem == half && (mant & 1ull))) {
+            ++mant;
+            if (mant >> 53) {
+                mant >>= 1;
+                ++sh;
+            }
+        }
+    } else {
+        mant = m << (-sh);
+    }
+    const int be = E + sh + 52 + 1023;  // value = mant 2^(E+sh), mant in [2^52, 2^53)
+    if (be <= 0 || be >= 2047) return ldexp(neg ? -(double)m : (double)m, E);  // outside the normal range
+    return __longlong_as_double((long long)((neg << 63) | ((unsigned long long)be << 52) | (mant & ((1ull << 52) - 1))));
+}
+
+// round(f * 2^k) as int64 from the FP32 bit pattern (|f 2^k| < 2^62)
+__device__ __forceinline__ long long f32_fixed(float f, int k) {
+    const unsigned b = __float_as_uint(f);
+    const int ex = (int)((b >> 23) & 0xff);
+    if (ex == 0) return 0;  // zero or FP32 denormal: far below the resolution kept
+    const long long mant = (long long)((b & 0x7fffff) | 0x800000);
+    const int sh = ex - 150 + k;  // f 2^k = mant 2^sh
+    long long v;
+    if (sh >= 0) v = mant << sh;
+    else if (sh <= -25) v = 0;
+    else v = (mant + (1ll << (-sh - 1))) >> (-sh);
+    return (b >> 31) ? -v : v;
+}
+
+// C = 2^(eA+eB-16) (S0 + S1/256 + F).  With T = 256 S0 + S1 (exact; |T| <
+// 2^39 for K <= 16384 per split) and F kept to 2^-28 of an S0 unit (below
+// 2^-44 of max|row| max|col|), Z = 2^20 T + round(2^28 F) is an exact int64
+// and C = Z 2^(eA+eB-44).  escale = eA + eB - 16.
+__device__ __forceinline__ double assemble(int S0, int S1, float F, int escale) {
+    const long long T = (long long)S0 * 256 + (long long)S1;
+    const long long Z = T * (1ll << 20) + __float2ll_rn(F * 268435456.0f);  // F 2^28 < 2^62
+    return i64_ldexp(Z, escale - 28);
+}
+
 // ---------------------------------------------------------------------------
 // slicing
 // ---------------------------------------------------------------------------
@@ -79,14 +207,15 @@ __device__ __forceinline__ __nv_bfloat16 slice_value(int digit, int t) {
     return __float2bfloat16_rn(ldexpf((float)digit, -8 * t));
 }
 
-// K contiguous (cs == 1): one warp per row.
-__global__ void k_split_rows(const double* __restrict__ X, int R, int K, int K8, long long rs, int s,
+// Consecutive k contiguous (innermost K stride 1): one warp per row.
+__global__ void k_split_rows(const double* __restrict__ X, int R, int K, int K8, View rv, View kv, int s,
                              __nv_bfloat16* __restrict__ out, int* __restrict__ ex) {
     const int warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5, lane = threadIdx.x & 31;
     if (warp >= R) return;
-    const double* x = X + (size_t)warp * rs;
+    const double* xr = X + view_offset32(rv, (unsigned)warp);
+    auto at = [&](int k) { return xr[kv.n == 1 ? (long long)k * kv.stride[0] : view_offset32(kv, (unsigned)k)]; };
     double mx = 0.0;
-    for (int k = lane; k < K; k += 32) mx = fmax(mx, fabs(x[k]));
+    for (int k = lane; k < K; k += 32) mx = fmax(mx, fabs(at(k)));
     for (int o = 16; o > 0; o >>= 1) mx = fmax(mx, __shfl_xor_sync(0xffffffffu, mx, o));
     const int e = row_exponent(mx);
     if (lane == 0) ex[warp] = e;
@@ -94,7 +223,7 @@ __global__ void k_split_rows(const double* __restrict__ X, int R, int K, int K8,
     __nv_bfloat16* o = out + (size_t)warp * K8;
     for (int k = lane; k < K8; k += 32) {
         int d[MAX_S];
-        if (k < K) digits(x[k], e, s, d);
+        if (k < K) digits(at(k), e, s, d);
         else
             for (int t = 0; t < MAX_S; ++t) d[t] = 0;
         for (int t = 0; t < s; ++t) o[t * plane + k] = slice_value(d[t], t);
@@ -108,18 +237,35 @@ __global__ void k_split_rows(const double* __restrict__ X, int R, int K, int K8,
 // through shared memory so that the K-major slice writes coalesce too.
 constexpr int COLS_KRANGE = 256;
 
-__global__ void k_rowmax_cols(const double* __restrict__ X, int R, int K, long long rs, long long cs,
+__global__ void k_rowmax_cols(const double* __restrict__ X, int R, int K, View rv, View kv, int kranges,
                               unsigned long long* __restrict__ maxbits) {
-    const int r = blockIdx.x * 32 + (threadIdx.x & 31);
-    const int k0 = (blockIdx.y * (blockDim.x >> 5) + (threadIdx.x >> 5)) * COLS_KRANGE;
+    const int w = (blockIdx.x * blockDim.x + threadIdx.x) >> 5, lane = threadIdx.x & 31;
+    const int rg = w / kranges, kr = w - rg * kranges;
+    const int r = rg * 32 + lane;
+    const int k0 = kr * COLS_KRANGE;
     if (r >= R || k0 >= K) return;
     const int k1 = min(K, k0 + COLS_KRANGE);
+    const double* xr = X + view_offset32(rv, (unsigned)r);
+    Odometer od;
+    od.init(kv, (unsigned)k0);
     double mx = 0.0;
-    for (int k = k0; k < k1; ++k) mx = fmax(mx, fabs(X[(size_t)r * rs + (size_t)k * cs]));
+    for (int k = k0; k < k1; k += 8) {
+        long long off[8];
+#pragma unroll
+        for (int u = 0; u < 8; ++u) {
+            off[u] = od.off;
+            if (k + u + 1 < k1) od.step(kv);
+        }
+        double v[8];
+#pragma unroll
+        for (int u = 0; u < 8; ++u) v[u] = (k + u < k1) ? xr[off[u]] : 0.0;
+#pragma unroll
+        for (int u = 0; u < 8; ++u) mx = fmax(mx, fabs(v[u]));
+    }
     atomicMax(maxbits + r, (unsigned long long)__double_as_longlong(mx));
 }
 
-__global__ void k_split_cols(const double* __restrict__ X, int R, int K, int K8, long long rs, long long cs,
+__global__ void k_split_cols(const double* __restrict__ X, int R, int K, int K8, View rv, View kv,
                              int s, const unsigned long long* __restrict__ maxbits, __nv_bfloat16* __restrict__ out,
                              int* __restrict__ ex) {
     __shared__ __nv_bfloat16 tile[2][MAX_S][32][33];  // launched with 2 warps
@@ -131,13 +277,26 @@ __global__ void k_split_cols(const double* __restrict__ X, int R, int K, int K8,
     const bool live = r < R;
     const int e = live ? row_exponent(__longlong_as_double((long long)maxbits[r])) : 0;
     if (live && k0 == 0) ex[r] = e;
-    for (int kk = 0; kk < 32; ++kk) {
-        const int k = k0 + kk;
-        int d[MAX_S];
-        if (live && k < K) digits(X[(size_t)r * rs + (size_t)k * cs], e, s, d);
-        else
-            for (int t = 0; t < MAX_S; ++t) d[t] = 0;
-        for (int t = 0; t < s; ++t) tile[w][t][lane][kk] = slice_value(d[t], t);
+    const double* xr = X + (live ? view_offset32(rv, (unsigned)r) : 0);
+    Odometer od;
+    od.init(kv, (unsigned)min(k0, K - 1));
+    for (int kb = 0; kb < 32; kb += 8) {
+        double v[8];
+#pragma unroll
+        for (int u = 0; u < 8; ++u) {
+            const int k = k0 + kb + u;
+            v[u] = 0.0;
+            if (live && k < K) {
+                v[u] = xr[od.off];
+                od.step(kv);
+            }
+        }
+#pragma unroll
+        for (int u = 0; u < 8; ++u) {
+            int d[MAX_S];
+            digits(v[u], e, s, d);
+            for (int t = 0; t < s; ++t) tile[w][t][lane][kb + u] = slice_value(d[t], t);
+        }
     }
     __syncwarp();
     const size_t plane = (size_t)R * K8;
@@ -162,14 +321,16 @@ __device__ __forceinline__ void mbar_expect_tx(uint64_t* bar, uint32_t bytes) {
 __device__ __forceinline__ void mbar_arrive(uint64_t* bar) {
     asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(bar)) : "memory");
 }
+// try_wait with a suspend-time hint: the thread sleeps in hardware until the
+// phase completes or ~20 us pass, instead of spinning on issue slots
 __device__ __forceinline__ bool mbar_try_wait(uint64_t* bar, uint32_t parity) {
     uint32_t ok;
     asm volatile(
         "{\n\t.reg .pred p;\n\t"
-        "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+        "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2, %3;\n\t"
         "selp.u32 %0, 1, 0, p;\n\t}"
         : "=r"(ok)
-        : "r"(smem_u32(bar)), "r"(parity)
+        : "r"(smem_u32(bar)), "r"(parity), "r"(20000u)
         : "memory");
     return ok != 0;
 }
@@ -251,7 +412,7 @@ struct GemmArgs {
     int direct;           // 1: write C; 0: write split-K partials
     double alpha, beta;
     double* C;
-    int ldc;
+    View out_r, out_c;    // C offset of (m, n) = view(out_r, m) + view(out_c, n)
     int* PS0;             // partials [z][Mpad][Npad]
     int* PS1;
     float* PF;
@@ -419,14 +580,21 @@ __global__ void __launch_bounds__(THREADS, 1)
                 const int b = grp + 3 * jb;
                 if (b >= NB16) continue;
                 if (g.direct) {
-                    if (m >= g.M) continue;
+                    // the 16 columns of this block are the same for every lane:
+                    // lane j works out column j's offset and exponent once
+                    const int nl = n0 + b * 16 + (lane & 15);
+                    const long long coff_l = nl < g.N ? view_offset32(g.out_c, (unsigned)nl) : 0;
+                    const int eb_l = nl < g.N ? g.eB[nl] : 0;
+                    double* crow = g.C + (m < g.M ? view_offset32(g.out_r, (unsigned)m) : 0);
 #pragma unroll
                     for (int j = 0; j < 16; ++j) {
+                        const long long coff = __shfl_sync(0xffffffffu, coff_l, j);
+                        const int eb = __shfl_sync(0xffffffffu, eb_l, j);
                         const int n = n0 + b * 16 + j;
-                        if (n >= g.N) continue;
-                        double v = (double)S0[jb][j] + ldexp((double)S1[jb][j], -8) + (double)F[jb][j];
-                        v = g.alpha * ldexp(v, ea + g.eB[n] - 16);
-                        double* cp = g.C + (size_t)m * g.ldc + n;
+                        if (m >= g.M || n >= g.N) continue;
+                        double v = assemble(S0[jb][j], S1[jb][j], F[jb][j], ea + eb - 16);
+                        if (g.alpha != 1.0) v *= g.alpha;
+                        double* cp = crow + coff;
                         *cp = (g.beta == 0.0) ? v : fma(g.beta, *cp, v);
                     }
                 } else {
@@ -453,21 +621,21 @@ __global__ void __launch_bounds__(THREADS, 1)
 __global__ void k_oz_combine(const int* __restrict__ PS0, const int* __restrict__ PS1, const float* __restrict__ PF,
                              int splits, int Mpad, int Npad, int M, int N, const int* __restrict__ eA,
                              const int* __restrict__ eB, double alpha, double beta, double* __restrict__ C,
-                             int ldc) {
+                             View out_r, View out_c) {
     const size_t total = (size_t)M * N;
     for (size_t t = blockIdx.x * (size_t)blockDim.x + threadIdx.x; t < total; t += (size_t)gridDim.x * blockDim.x) {
         const int m = (int)(t / N), n = (int)(t % N);
-        long long s0 = 0, s1 = 0;
-        double f = 0.0;
+        // split-K runs only for small outputs: FP64 sums here are cheap and
+        // cannot overflow however many splits there are
+        double v = 0.0;
         for (int z = 0; z < splits; ++z) {
             const size_t idx = ((size_t)z * Mpad + m) * Npad + n;
-            s0 += PS0[idx];
-            s1 += PS1[idx];
-            f += (double)PF[idx];
+            const long long T = (long long)PS0[idx] * 256 + (long long)PS1[idx];
+            v += (double)T + (double)(PF[idx] * 256.0f);
         }
-        double v = (double)s0 + ldexp((double)s1, -8) + f;
-        v = alpha * ldexp(v, eA[m] + eB[n] - 16);
-        double* cp = C + (size_t)m * ldc + n;
+        v = scale_pow2(v, eA[m] + eB[n] - 24);
+        if (alpha != 1.0) v *= alpha;
+        double* cp = C + view_offset32(out_r, (unsigned)m) + view_offset32(out_c, (unsigned)n);
         *cp = (beta == 0.0) ? v : fma(beta, *cp, v);
     }
 }
@@ -519,7 +687,9 @@ struct Plan {
 
 Plan plan_of(int M, int N, int K, int s) {
     Plan p{};
-    p.nb16 = N <= 144 ? (N + 15) / 16 : 8;
+    // fewest 144-wide tiles, then the narrowest 16-multiple width that covers N
+    const int nt = (N + 143) / 144;
+    p.nb16 = ((N + nt - 1) / nt + 15) / 16;
     if (p.nb16 < 1) p.nb16 = 1;
     p.bn = 16 * p.nb16;
     p.m_tiles = (M + oz::BM - 1) / oz::BM;
@@ -571,7 +741,24 @@ inline const int* split_exponents(const void* buf, int R, int K8, int s) {
 }
 
 cudaError_t oz_split(const double* X, int R, int K, long long rs, long long cs, int s, void* buf, cudaStream_t st) {
-    if (R <= 0 || K <= 0 || s < 2 || s > oz::MAX_S) return cudaErrorInvalidValue;
+    OzView rv{1, {R, 1, 1, 1}, {rs, 0, 0, 0}}, kv{1, {K, 1, 1, 1}, {cs, 0, 0, 0}};
+    return oz_split_view(X, R, K, rv, kv, s, buf, st);
+}
+
+cudaError_t oz_split_view(const double* X, int R, int K, const OzView& rvh, const OzView& kvh, int s, void* buf,
+                          cudaStream_t st) {
+    if (R <= 0 || K <= 0 || s < 2 || s > oz::MAX_S || rvh.n < 1 || rvh.n > 4 || kvh.n < 1 || kvh.n > 4)
+        return cudaErrorInvalidValue;
+    oz::View rv, kv;
+    rv.n = rvh.n;
+    kv.n = kvh.n;
+    for (int a = 0; a < 4; ++a) {
+        rv.dim[a] = rvh.dim[a];
+        rv.stride[a] = rvh.stride[a];
+        kv.dim[a] = kvh.dim[a];
+        kv.stride[a] = kvh.stride[a];
+    }
+    const long long cs = kv.stride[kv.n - 1];
     const int K8 = k8_of(K);
     __nv_bfloat16* sl = (__nv_bfloat16*)buf;
     unsigned long long* mb = (unsigned long long*)((char*)buf + align256((size_t)s * R * K8 * 2));
@@ -579,17 +766,18 @@ cudaError_t oz_split(const double* X, int R, int K, long long rs, long long cs, 
     if (cs == 1) {
         ++g_launches;
         const unsigned blocks = (unsigned)(((size_t)R * 32 + 255) / 256);
-        oz::k_split_rows<<<blocks, 256, 0, st>>>(X, R, K, K8, rs, s, sl, ex);
+        oz::k_split_rows<<<blocks, 256, 0, st>>>(X, R, K, K8, rv, kv, s, sl, ex);
     } else {
         cudaError_t e = cudaMemsetAsync(mb, 0, (size_t)R * 8, st);
         if (e != cudaSuccess) return e;
         const unsigned rg = (unsigned)((R + 31) / 32);
         const unsigned kr = (unsigned)((K + oz::COLS_KRANGE - 1) / oz::COLS_KRANGE);
-        if ((kr + 3) / 4 > 65535u || (K8 / 32 + 2) / 2 > 65535) return cudaErrorInvalidValue;
+        const unsigned long long warps = (unsigned long long)rg * kr;
+        if ((warps + 3) / 4 > 0x7fffffffull || (K8 / 32 + 2) / 2 > 65535) return cudaErrorInvalidValue;
         ++g_launches;
-        oz::k_rowmax_cols<<<dim3(rg, (kr + 3) / 4), 128, 0, st>>>(X, R, K, rs, cs, mb);
+        oz::k_rowmax_cols<<<(unsigned)((warps + 3) / 4), 128, 0, st>>>(X, R, K, rv, kv, (int)kr, mb);
         ++g_launches;
-        oz::k_split_cols<<<dim3(rg, (unsigned)((K8 / 32 + 1 + 1) / 2)), 64, 0, st>>>(X, R, K, K8, rs, cs, s, mb, sl, ex);
+        oz::k_split_cols<<<dim3(rg, (unsigned)((K8 / 32 + 1 + 1) / 2)), 64, 0, st>>>(X, R, K, K8, rv, kv, s, mb, sl, ex);
     }
     return cudaGetLastError();
 }
@@ -598,6 +786,13 @@ size_t oz_gemm_ws_bytes(int M, int N, int K, int s) { return plan_of(M, N, K, s)
 
 cudaError_t oz_gemm(int M, int N, int K, int s, const void* Asplit, const void* Bsplit, double alpha, double beta,
                     double* C, int ldc, void* ws, size_t ws_bytes, int* err, cudaStream_t st) {
+    OzView r{1, {M, 1, 1, 1}, {ldc, 0, 0, 0}}, c{1, {N, 1, 1, 1}, {1, 0, 0, 0}};
+    return oz_gemm_view(M, N, K, s, Asplit, Bsplit, alpha, beta, C, r, c, ws, ws_bytes, err, st);
+}
+
+cudaError_t oz_gemm_view(int M, int N, int K, int s, const void* Asplit, const void* Bsplit, double alpha,
+                         double beta, double* C, const OzView& orv, const OzView& ocv, void* ws, size_t ws_bytes,
+                         int* err, cudaStream_t st) {
     if (M <= 0 || N <= 0) return cudaSuccess;
     if (K <= 0 || s < 2 || s > oz::MAX_S) return cudaErrorInvalidValue;
     const Plan p = plan_of(M, N, K, s);
@@ -621,7 +816,14 @@ cudaError_t oz_gemm(int M, int N, int K, int s, const void* Asplit, const void* 
     g.alpha = alpha;
     g.beta = beta;
     g.C = C;
-    g.ldc = ldc;
+    g.out_r.n = orv.n;
+    g.out_c.n = ocv.n;
+    for (int a = 0; a < 4; ++a) {
+        g.out_r.dim[a] = orv.dim[a];
+        g.out_r.stride[a] = orv.stride[a];
+        g.out_c.dim[a] = ocv.dim[a];
+        g.out_c.stride[a] = ocv.stride[a];
+    }
     g.Mpad = p.m_tiles * oz::BM;
     g.Npad = p.n_tiles * p.bn;
     if (!g.direct) {
@@ -648,7 +850,7 @@ cudaError_t oz_gemm(int M, int N, int K, int s, const void* Asplit, const void* 
     if (blocks > 152 * 16) blocks = 152 * 16;
     ++g_launches;
     oz::k_oz_combine<<<(unsigned)blocks, 256, 0, st>>>(g.PS0, g.PS1, g.PF, p.ksplit, g.Mpad, g.Npad, M, N, g.eA,
-                                                        g.eB, alpha, beta, C, ldc);
+                                                        g.eB, alpha, beta, C, g.out_r, g.out_c);
     return cudaGetLastError();
 }
 

@@ -35,15 +35,16 @@ ENV_INDEX = {"C1": 0, "T1": 1, "C2": 2, "T2": 3, "C3": 4, "T3": 5, "C4": 6, "T4"
 class ctm_options(ctypes.Structure):
     _fields_ = [("chi", c_int), ("max_sweeps", c_int), ("tol", c_double), ("precision", c_int),
                 ("ozaki_slices", c_int), ("rsvd_oversample", c_int), ("rsvd_power_iters", c_int),
-                ("sv_cutoff_rel", c_double), ("seed", ctypes.c_uint64), ("exact_svd_max_n", c_int)]
+                ("sv_cutoff_rel", c_double), ("seed", ctypes.c_uint64), ("exact_svd_max_n", c_int),
+                ("rsvd_warm_start", c_int)]
 
 
 class ctm_profile_data(ctypes.Structure):
-    _fields_ = [("ms", c_double * 4), ("flops", c_double * 4), ("bytes", c_double * 4),
-                ("calls", ctypes.c_longlong * 4)]
+    _fields_ = [("ms", c_double * 8), ("flops", c_double * 8), ("bytes", c_double * 8),
+                ("calls", ctypes.c_longlong * 8)]
 
 
-PROFILE_CLASSES = ("gemm", "permute", "qr", "svd")
+PROFILE_CLASSES = ("gemm", "permute", "qr", "svd", "split")
 
 
 def _sig(name, res, *args):
@@ -85,6 +86,7 @@ _sig("ctm_svd_noalloc", c_int, c_void_p, c_int, c_void_p, c_void_p, c_void_p, c_
 _sig("ctm_profile_enable", c_int, c_void_p, c_int)
 _sig("ctm_profile_read", c_int, c_void_p, ctypes.POINTER(ctm_profile_data), c_int)
 _sig("ctm_kernel_launches", ctypes.c_longlong)
+_sig("ctm_profile_report", c_int, c_void_p, c_char_p, c_size_t, c_int)
 
 EXPORTED = [n for n in dir(_lib) if n.startswith("ctm_")]
 
@@ -239,6 +241,13 @@ def ctm_profile_read(h, reset=False):
     _check(_lib.ctm_profile_read(h, ctypes.byref(p), int(reset)), h)
     return {c: dict(ms=p.ms[i], flops=p.flops[i], bytes=p.bytes[i], calls=p.calls[i])
             for i, c in enumerate(PROFILE_CLASSES)}
+
+
+def ctm_profile_report(h, reset=False):
+    import json
+    buf = ctypes.create_string_buffer(1 << 16)
+    _check(_lib.ctm_profile_report(h, buf, len(buf), int(reset)), h)
+    return json.loads(buf.value.decode())
 
 
 def ctm_kernel_launches():

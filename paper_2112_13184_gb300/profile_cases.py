@@ -29,7 +29,41 @@ def apply_fp64():
     print("apply_fp64 done", float(Y[0, 0]))
 
 
-CASES = {"apply_fp64": apply_fp64}
+def _oz(M, N, K, slices=5, tA=0):
+    import torch
+    from paper_2112_13184_gb300 import ctm
+    g = torch.Generator(device="cuda").manual_seed(0)
+    A = torch.randn((K, M) if tA else (M, K), dtype=torch.float64, device="cuda", generator=g)
+    B = torch.randn(K, N, dtype=torch.float64, device="cuda", generator=g)
+    C = torch.empty(M, N, dtype=torch.float64, device="cuda")
+    ws = torch.empty(ctm.ctm_gemm_ozaki_workspace_bytes(M, N, K, slices), dtype=torch.uint8, device="cuda")
+    for _ in range(3):
+        ctm.ctm_gemm_ozaki(tA, 0, M, N, K, 1.0, A, A.shape[1], B, N, 0.0, C, N, slices, ws)
+    torch.cuda.synchronize()
+    print("done", float(C[0, 0]))
+
+
+def apply_oz():
+    """Corner apply of the D=8, chi=128 sweep on the tensor cores (5 slices)."""
+    _oz(8192, 144, 8192)
+
+
+def x2_oz():
+    """First corner-formation product of the D=8, chi=128 sweep: 8192 x 8192 x 128."""
+    _oz(8192, 8192, 128)
+
+
+def x3_oz():
+    """Second corner-formation product of the D=8, chi=128 sweep: 1048576 x 192 x 64."""
+    _oz(1048576, 192, 64)
+
+
+def x4t_oz():
+    """Third product's shape with a transposed (column-layout) A: 1048576 x 64 x 192."""
+    _oz(1048576, 64, 192, tA=1)
+
+
+CASES = {"apply_fp64": apply_fp64, "apply_oz": apply_oz, "x2_oz": x2_oz, "x3_oz": x3_oz, "x4t_oz": x4t_oz}
 
 if __name__ == "__main__":
     if len(sys.argv) != 2 or sys.argv[1] not in CASES:
