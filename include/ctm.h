@@ -61,7 +61,7 @@ typedef enum {
     CTM_ERR_ARG = -1,        /* bad argument (size, index, null pointer)          */
     CTM_ERR_OOM = -2,        /* device allocation failed                          */
     CTM_ERR_CUDA = -3,       /* a CUDA call failed                                */
-    CTM_ERR_NONFINITE = -4,  /* NaN/Inf appeared in the environment               */
+    CTM_ERR_NONFINITE = -4,  /* NaN/Inf (or an all-zero tensor) in the environment */
     CTM_ERR_TIMEOUT = -5,    /* a bounded device wait gave up                     */
     CTM_ERR_STATE = -6       /* call out of order (e.g. no tensors set)           */
 } ctm_status;

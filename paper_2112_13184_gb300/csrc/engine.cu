@@ -198,7 +198,7 @@ size_t footprint(int d, int D, const ctm_options& o) {
     dbl += 4 * z.Nchi;               // Pup, PdnT
     dbl += 6 * z.Nk;                 // Om, Y, Z, Qm, Qm2, Qb
     dbl += 4 * z.kk + 2 * (size_t)k; // Rb, G, Us, Ws, Sv, inv
-    dbl += 4 * z.Nchi;               // Uc, Vc, t1, t2
+    dbl += z.Nchi + 3 * std::max(z.Nk, z.Nchi);  // Uc; Vc, t1, t2
     dbl += 5 * z.kk + k + z.Nk;      // Cholesky-QR scratch
     dbl += 2 * z.C + 2 * z.T;        // newC1, newC4, newT4, tmpT
     dbl += 2 * z.Nchi * d * d;       // Lh, Rh
@@ -380,26 +380,56 @@ ctm_status qr_(ctm_ctx* h, const double* Y, double* Q, double* R) {
     prof_end(h, ev, P_QR, 4.0 * h->N * (double)h->k * h->k, 0.0);
     return CTM_OK;
 }
+// G = Y^T Y (k x k) of an N x k basis, always in FP64
+ctm_status gram(ctm_ctx* h, const double* Y, double* G) {
+    const int N = h->N, k = h->k;
+    const size_t ev = prof_begin(h);
+    CK(ctm::dgemm(true, false, k, k, N, 1.0, Y, k, Y, k, 0.0, G, k, h->stream, h->splitk, h->splitk_n));
+    prof_end(h, ev, P_GEMM, 2.0 * k * (double)k * N, 8.0 * ((double)N * k + (double)k * k));
+    return CTM_OK;
+}
+
 // Column-equilibrated Cholesky QR, two passes (CholQR2): for the bases of a
 // warm-started range finder, whose columns are close to orthogonal with
 // graded norms, it is as accurate as Householder and is GEMM work.
-//   G = Y^T Y, D = diag(G)^1/2, D^-1 G D^-1 = R1'^T R1', Q1 = Y D^-1 R1'^-1,
-//   Q1^T Q1 = R2^T R2, Q = Q1 R2^-1, R = R2 R1' D.
+//   G = Y^T Y, D ~ diag(G)^1/2 (powers of two), D^-1 G D^-1 = R1'^T R1',
+//   Q1 = Y D^-1 R1'^-1, Q1^T Q1 + s2 I = R2^T R2, Q = Q1 R2^-1, R = R2 R1' D.
+// Both passes shift the diagonal by 1e-14 of its mean: a warm basis of a
+// low-rank M has columns that M maps to rounding noise, Q1 then has a
+// condition number near 1/sqrt(shift), and an unshifted second pass meets
+// negative pivots.  The shift leaves Q orthonormal to ~1e-14 on every
+// direction M resolves and shortens only the noise columns, which the
+// singular-value cutoff removes.  Both Gram matrices are formed in FP64
+// whatever the precision: the shift keeps the factorisation positive only
+// while G is accurate to about that level, and an emulated Gram (error
+// ~2^-27 |y_i||y_j|) is not.
 ctm_status qr_chol(ctm_ctx* h, const double* Y, double* Q, double* R) {
     ProfTag tg(h, "qr");
-    const size_t ev = prof_begin(h);
     const int N = h->N, k = h->k;
-    CKS(gemm(h, true, false, k, k, N, Y, k, Y, k, h->cq_G, k));
-    CK(ctm::equilibrate(h->cq_G, k, h->cq_d, h->stream));
-    CK(ctm::chol_inv(h->cq_G, k, 1e-14, h->cq_R1, h->cq_R1i, h->stream));
-    CK(ctm::scale_rc(h->cq_R1i, k, h->cq_d, true, true, h->stream));  // D^-1 R1'^-1
+    const double kk = (double)k * k * k;
+    CKS(gram(h, Y, h->cq_G));
+    {
+        ProfTag t1(h, "qr.chol1");
+        const size_t ev = prof_begin(h);
+        CK(ctm::equilibrate(h->cq_G, k, h->cq_d, h->stream));
+        CK(ctm::chol_inv(h->cq_G, k, 1e-14, h->cq_R1, h->cq_R1i, h->stream));
+        CK(ctm::scale_rc(h->cq_R1i, k, h->cq_d, true, true, h->stream));  // D^-1 R1'^-1
+        prof_end(h, ev, P_QR, 2.0 * kk / 3.0, 0.0);
+    }
     CKS(gemm(h, false, false, N, k, k, Y, k, h->cq_R1i, k, h->cq_Q1, k));
-    CKS(gemm(h, true, false, k, k, N, h->cq_Q1, k, h->cq_Q1, k, h->cq_G, k));
-    CK(ctm::chol_inv(h->cq_G, k, 0.0, h->cq_R2, h->cq_R2i, h->stream));
+    CKS(gram(h, h->cq_Q1, h->cq_G));
+    {
+        ProfTag t2(h, "qr.chol2");
+        const size_t ev = prof_begin(h);
+        CK(ctm::chol_inv(h->cq_G, k, 1e-14, h->cq_R2, h->cq_R2i, h->stream));
+        prof_end(h, ev, P_QR, 2.0 * kk / 3.0, 0.0);
+    }
     CKS(gemm(h, false, false, N, k, k, h->cq_Q1, k, h->cq_R2i, k, Q, k));
+    ProfTag t3(h, "qr.r");
+    const size_t ev = prof_begin(h);
     CK(ctm::scale_rc(h->cq_R1, k, h->cq_d, false, false, h->stream));  // R1' D
     CK(ctm::dgemm(false, false, k, k, k, 1.0, h->cq_R2, k, h->cq_R1, k, 0.0, R, k, h->stream));
-    prof_end(h, ev, P_QR, 8.0 * N * (double)k * k, 0.0);
+    prof_end(h, ev, P_QR, 2.0 * kk, 0.0);
     return CTM_OK;
 }
 
@@ -521,19 +551,20 @@ ctm_status projectors(ctm_ctx* h, int slot, int cut) {
     CKS(applyMT(h, h->Qm, h->Zb, k));
     if (chol) CKS(qr_chol(h, h->Zb, h->Qb, h->Rb));
     else CKS(qr_(h, h->Zb, h->Qb, h->Rb));
-    if (warm_on) {
-        CK(cudaMemcpyAsync(h->warmV[cut], h->Qb, (size_t)N * k * sizeof(double), cudaMemcpyDeviceToDevice,
-                           h->stream));
-        h->warm_valid[cut] = true;
-    }
     CKS(perm(h, h->Rb, h->G, {k, k}, {1, 0}));
     CKS(svd_(h));
-    // U = Q U'[:, :chi], V = Q_b W[:, :chi]
+    // U = Q U'[:, :chi].  V = Q_b W over all k columns, sorted by singular
+    // value: its first chi columns are the projector's V, and the whole basis
+    // (the span of Q_b) starts this cut's range finder in the next sweep,
+    // where it leaves R_b close to diagonal once the environment settles, so
+    // that the Jacobi SVD starts near its quadratic phase.
+    double* Vf = warm_on ? h->warmV[cut] : h->Vc;
     CKS(gemm(h, false, false, N, chi, k, h->Qm, k, h->Us, k, h->Uc, chi));
-    CKS(gemm(h, false, false, N, chi, k, h->Qb, k, h->Ws, k, h->Vc, chi));
+    CKS(gemm(h, false, false, N, k, k, h->Qb, k, h->Ws, k, Vf, k));
+    if (warm_on) h->warm_valid[cut] = true;
     CK(ctm::inv_sqrt_cut(h->Sv, h->inv, chi, h->opt.sv_cutoff_rel, h->stream));
     // P_up = E_bl^T (E_br^T V) S^-1/2 ; P_dn^T = E_ul (E_ur U) S^-1/2
-    CKS(gemm(h, true, false, N, chi, N, h->E[2], N, h->Vc, chi, h->t1, chi));
+    CKS(gemm(h, true, false, N, chi, N, h->E[2], N, Vf, k, h->t1, chi));
     CKS(gemm(h, true, false, N, chi, N, h->E[3], N, h->t1, chi, h->Pup[slot], chi));
     CK(ctm::scale_cols(h->Pup[slot], N, chi, chi, h->inv, h->stream));
     CKS(gemm(h, false, false, N, chi, N, h->E[1], N, h->Uc, chi, h->t1, chi));
@@ -638,6 +669,10 @@ ctm_status read_flag(ctm_ctx* h) {
     if (f[1]) {
         h->err = "a bounded wait inside a tensor-core GEMM gave up";
         return CTM_ERR_TIMEOUT;
+    }
+    if (f[0] == 2) {
+        h->err = "an environment tensor became zero (every projector direction was cut)";
+        return CTM_ERR_NONFINITE;
     }
     if (f[0]) {
         h->err = "non-finite environment";
@@ -848,7 +883,7 @@ ctm_status ctm_create(int d, int D, const ctm_options* o, void* stream, ctm_hand
     A_(&h->Rb, z.kk); A_(&h->G, z.kk); A_(&h->Us, z.kk); A_(&h->Ws, z.kk);
     A_(&h->Sv, h->k); A_(&h->inv, h->k);
     const size_t tk = std::max(z.Nk, z.Nchi);
-    A_(&h->Uc, z.Nchi); A_(&h->Vc, z.Nchi); A_(&h->t1, tk); A_(&h->t2, tk);
+    A_(&h->Uc, z.Nchi); A_(&h->Vc, z.Nk); A_(&h->t1, tk); A_(&h->t2, tk);
     A_(&h->cq_G, z.kk); A_(&h->cq_R1, z.kk); A_(&h->cq_R1i, z.kk); A_(&h->cq_R2, z.kk); A_(&h->cq_R2i, z.kk);
     A_(&h->cq_d, h->k); A_(&h->cq_Q1, z.Nk);
     A_(&h->newC1, z.C); A_(&h->newC4, z.C); A_(&h->newT4, z.T); A_(&h->tmpT, z.T);

@@ -263,7 +263,10 @@ __global__ void k_scale_by_max(double* x, size_t n, const unsigned long long* ma
         return;
     }
     const double m = __longlong_as_double((long long)b);
-    if (m == 0.0) return;
+    if (m == 0.0) {  // an all-zero tensor: the projectors have collapsed
+        if (blockIdx.x == 0 && threadIdx.x == 0) atomicCAS(flag, 0, 2);
+        return;
+    }
     const double inv = 1.0 / m;
     for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x)
         x[i] *= inv;

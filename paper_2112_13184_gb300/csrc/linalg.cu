@@ -203,7 +203,7 @@ __global__ void __launch_bounds__(256) k_jacobi_cluster(double* __restrict__ Gt,
                     bb += __shfl_xor_sync(0xffffffffu, bb, o);
                     c += __shfl_xor_sync(0xffffffffu, c, o);
                 }
-                if (a == 0.0 || bb == 0.0) continue;
+                if (a < 1e-280 || bb < 1e-280) continue;  // zero or near underflow: nothing to rotate
                 const double rel = fabs(c) / (sqrt(a) * sqrt(bb));
                 if (lane == 0) atomicMax(offb + sw, (unsigned long long)__double_as_longlong(rel));
                 if (!(rel > tol)) continue;
@@ -237,74 +237,113 @@ __global__ void __launch_bounds__(256) k_jacobi_cluster(double* __restrict__ Gt,
 // Cholesky factor and its inverse of a small SPD matrix (one CTA, k <= 160,
 // the matrix in shared memory).  G + shift I = R^T R with R upper triangular
 // and positive diagonal; pivots below 1e-30 of the mean diagonal are clamped.
-// Lower triangle of S holds L = R^T (diagonal kept apart), the upper triangle
-// receives L^{-1} transposed = R^{-1}, column by column (one warp each).
+//
+// GB300 issues FP64 at a small fraction of its FP32 rate, so the kernel is
+// organised around few FP64 instructions and one barrier per step:
+//  - right-looking upper Cholesky on the unscaled rows: step j subtracts
+//    S[j][a] S[j][b] / piv_j from the trailing upper triangle, one warp per
+//    row a, lanes along b (contiguous, conflict-free); rows are scaled by
+//    1/sqrt(piv) once at the end;
+//  - the next pivot's 1/sqrt is taken by the lane that has just updated it:
+//    a single-precision estimate refined by two Newton steps for 1/sqrt(p),
+//    r <- r (3 - p r^2) / 2;
+//  - L^-1 (L = R^T) by right-looking substitution B_m -= (R_im / R_ii) B_i
+//    in the lower triangle (B = I initially, X_i = B_i / R_ii), again one
+//    warp per row; R^-1 = (L^-1)^T.
 // ---------------------------------------------------------------------------
+// 1/sqrt(p) for a normal p > 0: p = m 4^h with m in [1, 4) taken from the
+// exponent field, seed rsqrtf(m) 2^-h, then two Newton steps
+__device__ __forceinline__ double rsqrt_newton(double p) {
+    const long long bits = __double_as_longlong(p);
+    const int h = ((int)((bits >> 52) & 0x7ff) - 1023) >> 1;
+    const double m = __longlong_as_double(bits - ((long long)(2 * h) << 52));
+    double r = __longlong_as_double(__double_as_longlong((double)rsqrtf((float)m)) - ((long long)h << 52));
+#pragma unroll
+    for (int it = 0; it < 2; ++it) r = r * fma(-0.5 * p, r * r, 1.5);
+    return r;
+}
+
 __global__ void __launch_bounds__(1024) k_chol_inv(const double* __restrict__ G, int k, double shift_rel,
                                                   double* __restrict__ R, double* __restrict__ Rinv) {
-    extern __shared__ double S[];  // k*k + k
-    double* dg = S + (size_t)k * k;
+    extern __shared__ double S[];   // k*k, then ri[k] = 1/R_jj, dg[k] = R_jj, rp[k] = 1/piv_j
+    double* ri = S + (size_t)k * k;
+    double* dg = ri + k;
+    double* rp = dg + k;
     __shared__ double sm[32];
-    const int tid = threadIdx.x, nt = blockDim.x;
+    __shared__ double clamp;
+    const int tid = threadIdx.x, nt = blockDim.x, warp = tid >> 5, lane = tid & 31, nw = nt >> 5;
     double tr = 0.0;
-    for (int i = tid; i < k * k; i += nt) {
-        S[i] = G[i];
-        if (i / k == i % k) tr += G[i];
+    for (int t = tid; t < k * k; t += nt) {
+        const int i = t / k, j = t - i * k;
+        const double v = j >= i ? G[t] : 0.0;  // upper triangle of the symmetric G, lower zeroed
+        S[t] = v;
+        if (i == j) tr += v;
     }
     tr = block_sum(tr, sm);
     const double mean = tr > 0.0 ? tr / k : 1.0;
     for (int i = tid; i < k; i += nt) S[(size_t)i * k + i] += shift_rel * mean;
+    if (tid == 0) clamp = 1e-30 * mean;
+    __syncthreads();
+    auto pivot = [&](int j) {
+        double p = S[(size_t)j * k + j];
+        if (!(p > clamp)) p = clamp;
+        const double r = rsqrt_newton(p);
+        ri[j] = r;
+        dg[j] = p * r;
+        rp[j] = r * r;
+    };
+    if (tid == 0) pivot(0);
     __syncthreads();
     for (int j = 0; j < k; ++j) {
-        double piv = S[(size_t)j * k + j];
-        if (!(piv > 1e-30 * mean)) piv = 1e-30 * mean;
-        const double d = sqrt(piv);
-        const double inv = 1.0 / d;
-        for (int i = j + 1 + tid; i < k; i += nt) S[(size_t)i * k + j] *= inv;
-        if (tid == 0) dg[j] = d;
-        __syncthreads();
-        const int m = k - j - 1;  // trailing lower triangle, m(m+1)/2 entries
-        for (int t = tid; t < m * (m + 1) / 2; t += nt) {
-            int i = (int)((sqrtf(8.0f * (float)t + 1.0f) - 1.0f) * 0.5f);  // row estimate, corrected below
-            while ((i + 1) * (i + 2) / 2 <= t) ++i;
-            while (i * (i + 1) / 2 > t) --i;
-            const int l = t - i * (i + 1) / 2;
-            const int ii = j + 1 + i, ll = j + 1 + l;
-            S[(size_t)ii * k + ll] -= S[(size_t)ii * k + j] * S[(size_t)ll * k + j];
+        const double* Sj = S + (size_t)j * k;
+        const double q = rp[j];
+        for (int a = j + 1 + warp; a < k; a += nw) {
+            const double f = Sj[a] * q;
+            double* Sa = S + (size_t)a * k;
+            for (int b = a + lane; b < k; b += 32) Sa[b] = fma(-f, Sj[b], Sa[b]);
+            if (a == j + 1 && lane == 0) pivot(a);  // this lane has just finished S[a][a]
         }
         __syncthreads();
     }
-    // L^{-1}: column c by forward substitution; X[i][c] stored at S[c][i] (i >= c)
-    const int warp = tid >> 5, lane = tid & 31, nw = nt >> 5;
-    for (int c = warp; c < k; c += nw) {
-        if (lane == 0) S[(size_t)c * k + c] = 1.0 / dg[c];
-        __syncwarp();
-        for (int i = c + 1; i < k; ++i) {
-            double acc = 0.0;
-            for (int m = c + lane; m < i; m += 32) acc = fma(S[(size_t)i * k + m], S[(size_t)c * k + m], acc);
-            for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
-            if (lane == 0) S[(size_t)c * k + i] = -acc / dg[i];
-            __syncwarp();
-        }
+    // R: upper rows scaled by 1/sqrt(piv), diagonal sqrt(piv)
+    for (int t = tid; t < k * k; t += nt) {
+        const int i = t / k, j = t - i * k;
+        if (j > i) S[t] *= ri[i];
+        else if (j == i) S[t] = dg[i];
     }
     __syncthreads();
+    // B (rows of L^-1 before their 1/R_ii scaling) in the zeroed strict lower triangle
+    for (int i = 0; i < k; ++i) {
+        const double* Si = S + (size_t)i * k;
+        const double rii = ri[i];
+        for (int m = i + 1 + warp; m < k; m += nw) {
+            const double g = Si[m] * rii;  // L[m][i] / L[i][i]
+            double* Sm = S + (size_t)m * k;
+            for (int c = lane; c <= i; c += 32) Sm[c] = fma(-g, c == i ? 1.0 : Si[c], Sm[c]);
+        }
+        __syncthreads();
+    }
     for (int t = tid; t < k * k; t += nt) {
-        const int i = t / k, j = t % k;
-        R[t] = j > i ? S[(size_t)j * k + i] : (j == i ? dg[i] : 0.0);  // R = L^T
-        Rinv[t] = j >= i ? S[t] : 0.0;                                 // R^{-1} = (L^{-1})^T
+        const int i = t / k, j = t - i * k;
+        R[t] = j >= i ? S[t] : 0.0;
+        // R^-1[i][j] = (L^-1)[j][i] = B[j][i] / R_jj
+        Rinv[t] = j > i ? S[(size_t)j * k + i] * ri[j] : (j == i ? ri[i] : 0.0);
     }
 }
 
-// d_i = sqrt(G_ii) (1 if 0); G <- D^-1 G D^-1
+// d_i = 2^floor(log2(G_ii) / 2) (1 for a zero or non-normal diagonal);
+// G <- D^-1 G D^-1, exact since D holds powers of two
 __global__ void k_equilibrate(double* __restrict__ G, int k, double* __restrict__ d) {
-    __shared__ double dd[1024];
+    __shared__ double rd[1024];
     for (int i = threadIdx.x; i < k; i += blockDim.x) {
         const double v = G[(size_t)i * k + i];
-        dd[i] = v > 0.0 ? sqrt(v) : 1.0;
-        d[i] = dd[i];
+        const int be = (int)((__double_as_longlong(v) >> 52) & 0x7ff);
+        const int e = (v > 0.0 && be > 0 && be < 2047) ? (be - 1023) >> 1 : 0;
+        d[i] = __longlong_as_double((long long)(1023 + e) << 52);
+        rd[i] = __longlong_as_double((long long)(1023 - e) << 52);
     }
     __syncthreads();
-    for (int t = threadIdx.x; t < k * k; t += blockDim.x) G[t] /= dd[t / k] * dd[t % k];
+    for (int t = threadIdx.x; t < k * k; t += blockDim.x) G[t] *= rd[t / k] * rd[t % k];
 }
 
 // X[i][j] *= (rows ? w[i] : w[j]) ; with inv, divide instead
@@ -353,7 +392,7 @@ __global__ void k_jacobi_round(double* __restrict__ Gt, double* __restrict__ Wt,
         bb += __shfl_xor_sync(0xffffffffu, bb, o);
         c += __shfl_xor_sync(0xffffffffu, c, o);
     }
-    if (a == 0.0 || bb == 0.0) return;
+    if (a < 1e-280 || bb < 1e-280) return;  // zero or near underflow: nothing to rotate
     const double rel = fabs(c) / (sqrt(a) * sqrt(bb));
     if (threadIdx.x == 0) atomicMax(off + (size_t)sweep * nb + b, (unsigned long long)__double_as_longlong(rel));
     if (!(rel > tol)) return;
@@ -440,7 +479,11 @@ __global__ void k_transpose_batch(const double* __restrict__ A, double* __restri
 }
 
 constexpr int JACOBI_MAX_SWEEPS = 12;
-constexpr double JACOBI_TOL = 1e-15;
+// A pair counts as orthogonal at |g_p.g_q| <= tol |g_p||g_q|.  The computed
+// cosine of two length-k columns carries rounding of about sqrt(k) 2^-53,
+// so the bound follows k (4 sqrt(k) eps, the one-sided Jacobi criterion of
+// LAPACK's dgesvj with a safety factor) and never goes below 1e-15.
+inline double jacobi_tol(int k) { return std::max(1e-15, 4.0 * std::sqrt((double)k) * 0x1p-53); }
 
 }  // namespace
 
@@ -514,7 +557,7 @@ cudaError_t jacobi(double* Gt, double* Wt, int k, int n, int nb, unsigned long l
         cfg.numAttrs = 1;
         ++g_launches;
         const cudaError_t e = cudaLaunchKernelEx(&cfg, k_jacobi_cluster, Gt, Wt, k, n, JACOBI_MAX_SWEEPS,
-                                                 JACOBI_TOL, off, csize);
+                                                 jacobi_tol(k), off, csize);
         if (e == cudaSuccess) return cudaSuccess;
         cudaGetLastError();
         --g_launches;
@@ -523,7 +566,7 @@ cudaError_t jacobi(double* Gt, double* Wt, int k, int n, int nb, unsigned long l
     for (int sw = 0; sw < JACOBI_MAX_SWEEPS; ++sw)
         for (int r = 0; r < n - 1; ++r) {
             ++g_launches;
-            k_jacobi_round<<<dim3(n / 2, nb), 32, 0, s>>>(Gt, Wt, k, n, r, sw, off, JACOBI_TOL);
+            k_jacobi_round<<<dim3(n / 2, nb), 32, 0, s>>>(Gt, Wt, k, n, r, sw, off, jacobi_tol(k));
         }
     return cudaGetLastError();
 }
@@ -617,11 +660,11 @@ cudaError_t svd_noalloc(const double* G, int k, double* U, double* S, double* V,
 
 cudaError_t chol_inv(const double* G, int k, double shift_rel, double* R, double* Rinv, cudaStream_t s) {
     if (k <= 0 || k > 160) return cudaErrorInvalidValue;
-    const size_t smem = sizeof(double) * ((size_t)k * k + k);
+    const size_t smem = sizeof(double) * ((size_t)k * k + 3 * k);
     static bool attr = false;
     if (!attr) {
         cudaError_t e = cudaFuncSetAttribute(k_chol_inv, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                             (int)(sizeof(double) * (160 * 160 + 160)));
+                                             (int)(sizeof(double) * (160 * 160 + 3 * 160)));
         if (e) return e;
         attr = true;
     }

@@ -168,14 +168,24 @@ __device__ __forceinline__ double assemble(int S0, int S1, float F, int escale) 
 // ---------------------------------------------------------------------------
 // slicing
 // ---------------------------------------------------------------------------
-// exponent e with max|x| < 2^e (0 for an all-zero row)
+__device__ __forceinline__ unsigned long long abs_bits(double x) {
+    return (unsigned long long)__double_as_longlong(x) & 0x7fffffffffffffffull;
+}
+__device__ __forceinline__ unsigned long long umax64(unsigned long long a, unsigned long long b) {
+    return a > b ? a : b;
+}
+// exponent e with max|x| < 2^e (0 for an all-zero row; 1025 when the row
+// holds an infinity or a NaN, which the products turn into NaN outputs)
 __device__ __forceinline__ int row_exponent(double mx) {
     if (mx == 0.0) return 0;
     const int E = (int)((__double_as_longlong(mx) >> 52) & 0x7ff);
     return E == 0 ? -1022 : E - 1022;
 }
 
-// signed base-256 digits of round(x * 2^(8s - e)); |x| <= 2^e
+// signed base-256 digits of round(x * 2^(8s - e)); |x| <= 2^e.  d[1..s-1]
+// lie in [-128, 127] (Y = 256 Y' + d with Y' = floor((Y + 128) / 256)), d[0]
+// carries the sign and the top.  Every index of d is static (unrolled over
+// MAX_S), so d stays in registers.
 __device__ __forceinline__ void digits(double x, int e, int s, int* d) {
     const unsigned long long b = (unsigned long long)__double_as_longlong(x);
     int ex = (int)((b >> 52) & 0x7ff);
@@ -194,17 +204,20 @@ __device__ __forceinline__ void digits(double x, int e, int s, int* d) {
 #pragma unroll
     for (int t = MAX_S - 1; t >= 1; --t) {
         if (t < s) {
-            const long long dd = ((Y + 128) & 255) - 128;
-            d[t] = (int)dd;
-            Y = (Y - dd) >> 8;
+            const long long Yn = (Y + 128) >> 8;
+            d[t] = (int)Y - ((int)Yn << 8);
+            Y = Yn;
+        } else {
+            d[t] = 0;
         }
     }
     d[0] = (int)Y;
 }
 
+// digit * 2^(-8t): at most 9 significant bits, exact in FP32 and BF16; the
+// power of two is built from its exponent field
 __device__ __forceinline__ __nv_bfloat16 slice_value(int digit, int t) {
-    // digit * 2^(-8t): at most 9 significant bits, exact in FP32 and BF16
-    return __float2bfloat16_rn(ldexpf((float)digit, -8 * t));
+    return __float2bfloat16_rn((float)digit * __int_as_float((127 - 8 * t) << 23));
 }
 
 // Consecutive k contiguous (innermost K stride 1): one warp per row.
@@ -214,10 +227,12 @@ __global__ void k_split_rows(const double* __restrict__ X, int R, int K, int K8,
     if (warp >= R) return;
     const double* xr = X + view_offset32(rv, (unsigned)warp);
     auto at = [&](int k) { return xr[kv.n == 1 ? (long long)k * kv.stride[0] : view_offset32(kv, (unsigned)k)]; };
-    double mx = 0.0;
-    for (int k = lane; k < K; k += 32) mx = fmax(mx, fabs(at(k)));
-    for (int o = 16; o > 0; o >>= 1) mx = fmax(mx, __shfl_xor_sync(0xffffffffu, mx, o));
-    const int e = row_exponent(mx);
+    // max |x| on the bit patterns: non-negative doubles order like integers,
+    // and the integer pipe is far faster than GB300's FP64 pipe
+    unsigned long long mb = 0;
+    for (int k = lane; k < K; k += 32) mb = umax64(mb, abs_bits(at(k)));
+    for (int o = 16; o > 0; o >>= 1) mb = umax64(mb, __shfl_xor_sync(0xffffffffu, mb, o));
+    const int e = row_exponent(__longlong_as_double((long long)mb));
     if (lane == 0) ex[warp] = e;
     const size_t plane = (size_t)R * K8;
     __nv_bfloat16* o = out + (size_t)warp * K8;
@@ -226,7 +241,9 @@ __global__ void k_split_rows(const double* __restrict__ X, int R, int K, int K8,
         if (k < K) digits(at(k), e, s, d);
         else
             for (int t = 0; t < MAX_S; ++t) d[t] = 0;
-        for (int t = 0; t < s; ++t) o[t * plane + k] = slice_value(d[t], t);
+#pragma unroll
+        for (int t = 0; t < MAX_S; ++t)
+            if (t < s) o[t * plane + k] = slice_value(d[t], t);
     }
 }
 
@@ -248,7 +265,7 @@ __global__ void k_rowmax_cols(const double* __restrict__ X, int R, int K, View r
     const double* xr = X + view_offset32(rv, (unsigned)r);
     Odometer od;
     od.init(kv, (unsigned)k0);
-    double mx = 0.0;
+    unsigned long long mx = 0;
     for (int k = k0; k < k1; k += 8) {
         long long off[8];
 #pragma unroll
@@ -260,9 +277,9 @@ __global__ void k_rowmax_cols(const double* __restrict__ X, int R, int K, View r
 #pragma unroll
         for (int u = 0; u < 8; ++u) v[u] = (k + u < k1) ? xr[off[u]] : 0.0;
 #pragma unroll
-        for (int u = 0; u < 8; ++u) mx = fmax(mx, fabs(v[u]));
+        for (int u = 0; u < 8; ++u) mx = umax64(mx, abs_bits(v[u]));
     }
-    atomicMax(maxbits + r, (unsigned long long)__double_as_longlong(mx));
+    atomicMax(maxbits + r, mx);
 }
 
 __global__ void k_split_cols(const double* __restrict__ X, int R, int K, int K8, View rv, View kv,
@@ -295,7 +312,9 @@ __global__ void k_split_cols(const double* __restrict__ X, int R, int K, int K8,
         for (int u = 0; u < 8; ++u) {
             int d[MAX_S];
             digits(v[u], e, s, d);
-            for (int t = 0; t < s; ++t) tile[w][t][lane][kb + u] = slice_value(d[t], t);
+#pragma unroll
+            for (int t = 0; t < MAX_S; ++t)
+                if (t < s) tile[w][t][lane][kb + u] = slice_value(d[t], t);
         }
     }
     __syncwarp();
@@ -304,6 +323,125 @@ __global__ void k_split_cols(const double* __restrict__ X, int R, int K, int K8,
     if (k < K8)
         for (int rr = 0; rr < 32 && r0 + rr < R; ++rr)
             for (int t = 0; t < s; ++t) out[t * plane + (size_t)(r0 + rr) * K8 + k] = tile[w][t][rr][lane];
+}
+
+// ---------------------------------------------------------------------------
+// Plain 2D operands (one row stride, one K stride): the slices of eight
+// consecutive k of one row are built in registers and written as one 16-byte
+// store per slice.
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ unsigned bf2_bits(float a, float b) {
+    const __nv_bfloat162 p = __floats2bfloat162_rn(a, b);  // a in the low half (lower address)
+    return *reinterpret_cast<const unsigned*>(&p);
+}
+__device__ __forceinline__ void slice8_store(const double* v, int e, int s, __nv_bfloat16* dst, size_t plane) {
+    int d[8][MAX_S];
+#pragma unroll
+    for (int u = 0; u < 8; ++u) digits(v[u], e, s, d[u]);
+#pragma unroll
+    for (int t = 0; t < MAX_S; ++t) {
+        if (t < s) {
+            const float sc = __int_as_float((127 - 8 * t) << 23);  // 2^(-8t)
+            uint4 q;
+            q.x = bf2_bits((float)d[0][t] * sc, (float)d[1][t] * sc);
+            q.y = bf2_bits((float)d[2][t] * sc, (float)d[3][t] * sc);
+            q.z = bf2_bits((float)d[4][t] * sc, (float)d[5][t] * sc);
+            q.w = bf2_bits((float)d[6][t] * sc, (float)d[7][t] * sc);
+            *reinterpret_cast<uint4*>(dst + t * plane) = q;
+        }
+    }
+}
+
+// K contiguous, rows at stride rs, K8 <= 4 * 8 * TPR: TPR threads per row,
+// each holding up to four 8-wide chunks (chunk c = j + i TPR) in registers,
+// so X is read once.  VEC: rows start on 16 bytes (16-byte loads).
+template <int TPR, bool VEC>
+__global__ void __launch_bounds__(256) k_split_rows_reg(const double* __restrict__ X, int R, int K, int K8,
+                                                       long long rs, int s, __nv_bfloat16* __restrict__ out,
+                                                       int* __restrict__ ex) {
+    constexpr int RPB = 256 / TPR;
+    __shared__ unsigned long long red[8];
+    const int g = threadIdx.x / TPR, j = threadIdx.x % TPR;
+    const int r = blockIdx.x * RPB + g;
+    const bool live = r < R;
+    const double* xr = X + (live ? (long long)r * rs : 0);
+    const int nch = K8 >> 3;
+    double v[4][8];
+    unsigned long long mb = 0;
+#pragma unroll
+    for (int i = 0; i < 4; ++i) {
+        const int c = j + i * TPR;
+        const int k0 = c * 8;
+        if (VEC && live && c < nch && k0 + 8 <= K) {
+            const double2* p2 = reinterpret_cast<const double2*>(xr + k0);
+#pragma unroll
+            for (int h = 0; h < 4; ++h) {
+                const double2 w = __ldcs(p2 + h);
+                v[i][2 * h] = w.x;
+                v[i][2 * h + 1] = w.y;
+            }
+        } else {
+#pragma unroll
+            for (int u = 0; u < 8; ++u) v[i][u] = (live && c < nch && k0 + u < K) ? __ldcs(xr + k0 + u) : 0.0;
+        }
+#pragma unroll
+        for (int u = 0; u < 8; ++u) mb = umax64(mb, abs_bits(v[i][u]));
+    }
+    if (TPR <= 32) {
+#pragma unroll
+        for (int o = TPR / 2; o > 0; o >>= 1) mb = umax64(mb, __shfl_xor_sync(0xffffffffu, mb, o));
+    } else {
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) mb = umax64(mb, __shfl_xor_sync(0xffffffffu, mb, o));
+        const int w = threadIdx.x >> 5;
+        if ((threadIdx.x & 31) == 0) red[w] = mb;
+        __syncthreads();
+        constexpr int WPR = TPR / 32;  // warps per row
+        mb = 0;
+#pragma unroll
+        for (int q = 0; q < WPR; ++q) mb = umax64(mb, red[g * WPR + q]);
+    }
+    if (!live) return;
+    const int e = row_exponent(__longlong_as_double((long long)mb));
+    if (j == 0) ex[r] = e;
+    const size_t plane = (size_t)R * K8;
+#pragma unroll
+    for (int i = 0; i < 4; ++i) {
+        const int c = j + i * TPR;
+        if (c < nch) slice8_store(v[i], e, s, out + (size_t)r * K8 + (size_t)c * 8, plane);
+    }
+}
+
+// Rows contiguous (row stride 1), K at stride cs: lane = row, sixteen
+// consecutive k per step (each load instruction reads 32 consecutive rows),
+// one warp per 32 rows x kspan k (kspan a multiple of 16); row maxima from
+// k_rowmax_cols.
+__global__ void __launch_bounds__(128) k_split_cols_reg(const double* __restrict__ X, int R, int K, int K8,
+                                                       long long cs, int s,
+                                                       const unsigned long long* __restrict__ maxbits,
+                                                       __nv_bfloat16* __restrict__ out, int* __restrict__ ex,
+                                                       int kspan, int kgroups) {
+    const int wid = (int)((blockIdx.x * (size_t)blockDim.x + threadIdx.x) >> 5), lane = threadIdx.x & 31;
+    const int rg = wid / kgroups, kg = wid - rg * kgroups;
+    if (rg * 32 >= R) return;
+    const int r = rg * 32 + lane;
+    const bool live = r < R;
+    const int e = live ? row_exponent(__longlong_as_double((long long)maxbits[r])) : 0;
+    if (live && kg == 0) ex[r] = e;
+    const size_t plane = (size_t)R * K8;
+    const int kend = min(K8, (kg + 1) * kspan);
+    // 16 k per step: each lane then writes whole 32-byte sectors of every
+    // slice row (two 16-byte stores back to back), never half sectors that
+    // L2 would have to merge with a read from DRAM
+    for (int k0 = kg * kspan; k0 < kend; k0 += 16) {
+        double v[16];
+#pragma unroll
+        for (int u = 0; u < 16; ++u) v[u] = (live && k0 + u < K) ? __ldcs(X + (long long)(k0 + u) * cs + r) : 0.0;
+        if (live) {
+            slice8_store(v, e, s, out + (size_t)r * K8 + k0, plane);
+            if (k0 + 8 < kend) slice8_store(v + 8, e, s, out + (size_t)r * K8 + k0 + 8, plane);
+        }
+    }
 }
 
 // ---------------------------------------------------------------------------
@@ -575,6 +713,7 @@ __global__ void __launch_bounds__(THREADS, 1)
         if (ok) {
             const int m = m0 + q * 32 + lane;
             const int ea = (g.direct && m < g.M) ? g.eA[m] : 0;
+            const bool unit_alpha = g.alpha == 1.0, zero_beta = g.beta == 0.0;
 #pragma unroll
             for (int jb = 0; jb < NBG; ++jb) {
                 const int b = grp + 3 * jb;
@@ -593,9 +732,10 @@ __global__ void __launch_bounds__(THREADS, 1)
                         const int n = n0 + b * 16 + j;
                         if (m >= g.M || n >= g.N) continue;
                         double v = assemble(S0[jb][j], S1[jb][j], F[jb][j], ea + eb - 16);
-                        if (g.alpha != 1.0) v *= g.alpha;
+                        if (ea > 1024 || eb > 1024) v = __longlong_as_double(0x7ff8000000000000ll);  // non-finite operand
+                        if (!unit_alpha) v *= g.alpha;
                         double* cp = crow + coff;
-                        *cp = (g.beta == 0.0) ? v : fma(g.beta, *cp, v);
+                        *cp = zero_beta ? v : fma(g.beta, *cp, v);
                     }
                 } else {
                     const size_t row = ((size_t)blockIdx.z * g.Mpad + m) * g.Npad + n0 + b * 16;
@@ -633,7 +773,8 @@ __global__ void k_oz_combine(const int* __restrict__ PS0, const int* __restrict_
             const long long T = (long long)PS0[idx] * 256 + (long long)PS1[idx];
             v += (double)T + (double)(PF[idx] * 256.0f);
         }
-        v = scale_pow2(v, eA[m] + eB[n] - 24);
+        v = (eA[m] > 1024 || eB[n] > 1024) ? __longlong_as_double(0x7ff8000000000000ll)  // non-finite operand
+                                           : scale_pow2(v, eA[m] + eB[n] - 24);
         if (alpha != 1.0) v *= alpha;
         double* cp = C + view_offset32(out_r, (unsigned)m) + view_offset32(out_c, (unsigned)n);
         *cp = (beta == 0.0) ? v : fma(beta, *cp, v);
@@ -740,6 +881,27 @@ inline const int* split_exponents(const void* buf, int R, int K8, int s) {
     return (const int*)((const char*)buf + align256((size_t)s * R * K8 * 2) + align256((size_t)R * 8));
 }
 
+template <int TPR>
+void launch_rows_reg_t(bool vec, unsigned blocks, cudaStream_t st, const double* X, int R, int K, int K8,
+                       long long rs, int s, __nv_bfloat16* sl, int* ex) {
+    if (vec) oz::k_split_rows_reg<TPR, true><<<blocks, 256, 0, st>>>(X, R, K, K8, rs, s, sl, ex);
+    else oz::k_split_rows_reg<TPR, false><<<blocks, 256, 0, st>>>(X, R, K, K8, rs, s, sl, ex);
+}
+void launch_split_rows_reg(int tpr, bool vec, unsigned blocks, cudaStream_t st, const double* X, int R, int K,
+                           int K8, long long rs, int s, __nv_bfloat16* sl, int* ex) {
+    switch (tpr) {
+        case 1: launch_rows_reg_t<1>(vec, blocks, st, X, R, K, K8, rs, s, sl, ex); break;
+        case 2: launch_rows_reg_t<2>(vec, blocks, st, X, R, K, K8, rs, s, sl, ex); break;
+        case 4: launch_rows_reg_t<4>(vec, blocks, st, X, R, K, K8, rs, s, sl, ex); break;
+        case 8: launch_rows_reg_t<8>(vec, blocks, st, X, R, K, K8, rs, s, sl, ex); break;
+        case 16: launch_rows_reg_t<16>(vec, blocks, st, X, R, K, K8, rs, s, sl, ex); break;
+        case 32: launch_rows_reg_t<32>(vec, blocks, st, X, R, K, K8, rs, s, sl, ex); break;
+        case 64: launch_rows_reg_t<64>(vec, blocks, st, X, R, K, K8, rs, s, sl, ex); break;
+        case 128: launch_rows_reg_t<128>(vec, blocks, st, X, R, K, K8, rs, s, sl, ex); break;
+        default: launch_rows_reg_t<256>(vec, blocks, st, X, R, K, K8, rs, s, sl, ex); break;
+    }
+}
+
 cudaError_t oz_split(const double* X, int R, int K, long long rs, long long cs, int s, void* buf, cudaStream_t st) {
     OzView rv{1, {R, 1, 1, 1}, {rs, 0, 0, 0}}, kv{1, {K, 1, 1, 1}, {cs, 0, 0, 0}};
     return oz_split_view(X, R, K, rv, kv, s, buf, st);
@@ -763,10 +925,32 @@ cudaError_t oz_split_view(const double* X, int R, int K, const OzView& rvh, cons
     __nv_bfloat16* sl = (__nv_bfloat16*)buf;
     unsigned long long* mb = (unsigned long long*)((char*)buf + align256((size_t)s * R * K8 * 2));
     int* ex = const_cast<int*>(split_exponents(buf, R, K8, s));
-    if (cs == 1) {
+    const int nch = K8 / 8;
+    if (cs == 1 && rv.n == 1 && kv.n == 1 && nch <= 4 * 256) {
+        int tpr = 1;
+        while (tpr * 4 < nch) tpr *= 2;
+        const bool vec = ((uintptr_t)X % 16 == 0) && (rv.stride[0] % 2 == 0);
+        const unsigned blocks = (unsigned)(((size_t)R * tpr + 255) / 256);
+        ++g_launches;
+        launch_split_rows_reg(tpr, vec, blocks, st, X, R, K, K8, rv.stride[0], s, sl, ex);
+    } else if (cs == 1) {
         ++g_launches;
         const unsigned blocks = (unsigned)(((size_t)R * 32 + 255) / 256);
         oz::k_split_rows<<<blocks, 256, 0, st>>>(X, R, K, K8, rv, kv, s, sl, ex);
+    } else if (rv.n == 1 && rv.stride[0] == 1 && kv.n == 1) {
+        cudaError_t e = cudaMemsetAsync(mb, 0, (size_t)R * 8, st);
+        if (e != cudaSuccess) return e;
+        const unsigned rg = (unsigned)((R + 31) / 32);
+        const unsigned kr = (unsigned)((K + oz::COLS_KRANGE - 1) / oz::COLS_KRANGE);
+        const unsigned long long warps = (unsigned long long)rg * kr;
+        const int kspan = 256, kgroups = (K8 + kspan - 1) / kspan;
+        const unsigned long long warps2 = (unsigned long long)rg * kgroups;
+        if ((warps + 3) / 4 > 0x7fffffffull || (warps2 + 3) / 4 > 0x7fffffffull) return cudaErrorInvalidValue;
+        ++g_launches;
+        oz::k_rowmax_cols<<<(unsigned)((warps + 3) / 4), 128, 0, st>>>(X, R, K, rv, kv, (int)kr, mb);
+        ++g_launches;
+        oz::k_split_cols_reg<<<(unsigned)((warps2 + 3) / 4), 128, 0, st>>>(X, R, K, K8, kv.stride[0], s, mb, sl, ex,
+                                                                            kspan, kgroups);
     } else {
         cudaError_t e = cudaMemsetAsync(mb, 0, (size_t)R * 8, st);
         if (e != cudaSuccess) return e;

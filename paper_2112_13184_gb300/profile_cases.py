@@ -63,7 +63,24 @@ def x4t_oz():
     _oz(1048576, 64, 192, tA=1)
 
 
-CASES = {"apply_fp64": apply_fp64, "apply_oz": apply_oz, "x2_oz": x2_oz, "x3_oz": x3_oz, "x4t_oz": x4t_oz}
+def split_e():
+    """Slicing of an enlarged corner E (8192 x 8192) as a row-layout operand
+    (E X) and as a column-layout one (E^T X), one emulated product each."""
+    import torch
+    from paper_2112_13184_gb300 import ctm
+    N, k, slices = 8192, 144, 5
+    g = torch.Generator(device="cuda").manual_seed(0)
+    E = torch.randn(N, N, dtype=torch.float64, device="cuda", generator=g)
+    X = torch.randn(N, k, dtype=torch.float64, device="cuda", generator=g)
+    Y = torch.empty(N, k, dtype=torch.float64, device="cuda")
+    ws = torch.empty(ctm.ctm_gemm_ozaki_workspace_bytes(N, k, N, slices), dtype=torch.uint8, device="cuda")
+    for tA in (0, 1):
+        ctm.ctm_gemm_ozaki(tA, 0, N, k, N, 1.0, E, N, X, k, 0.0, Y, k, slices, ws)
+    torch.cuda.synchronize()
+    print("split_e done", float(Y[0, 0]))
+
+
+CASES = {"split_e": split_e, "apply_fp64": apply_fp64, "apply_oz": apply_oz, "x2_oz": x2_oz, "x3_oz": x3_oz, "x4t_oz": x4t_oz}
 
 if __name__ == "__main__":
     if len(sys.argv) != 2 or sys.argv[1] not in CASES:

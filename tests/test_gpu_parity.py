@@ -96,6 +96,45 @@ def test_neel_d2_D3_chi16_emulated_fp64(ctm, slices, tol):
     c.close()
 
 
+def test_neel_d2_D3_chi16_emulated_fp64_randomised(ctm):
+    """Emulated FP64 through the warm-started randomised range finder (no
+    exact SVD): the warm sweeps orthonormalise their bases by Cholesky-QR2,
+    whose Gram matrices must stay accurate for the diagonal shift to keep
+    them positive.  Same |dE| <= 1e-8 bar as the exact-SVD path."""
+    w = I.workload("neel_d2_D3_chi16")
+    c, ref = run_both(ctm, w["As"], w["envs"], w["d"], w["D"], w["chi"], w["sweeps"],
+                      precision=ctm.CTM_OZAKI_BF16, ozaki_slices=5, exact_svd_max_n=0)
+    g = observables_gpu(c, w["op1"], w["op2"])
+    o = observables_oracle(ref, w["As"], w["op1"], w["op2"])
+    err = np.abs(g - o)
+    print(f"randomised, 5 slices: max |dO| = {err.max():.3e}")
+    assert err.max() < 1e-8, err
+    c.close()
+
+
+@pytest.mark.parametrize("precision", ["fp64", "mixed"])
+def test_product_state_randomised_warm(ctm, precision):
+    """A Neel product state has a rank-1 environment, so all but one column
+    of every warm range-finder basis lies in the null space of M: the
+    Cholesky-QR2 of the warm sweeps must stay finite and the observables
+    exact."""
+    As = I.neel_tensors(2, 3, 0.0, seed=0)
+    envs = I.random_env(16, [3] * 4, seed=1)
+    prec = ctm.CTM_OZAKI_BF16 if precision == "mixed" else ctm.CTM_FP64
+    c = ctm.CTMRG(2, 3, 16, precision=prec, exact_svd_max_n=0, rsvd_warm_start=1)
+    c.set_tensors(As)
+    c.set_envs(envs)
+    c.sweep(5)
+    sz = I.spin_ops(2)["Sz"]
+    tol = 1e-12 if precision == "fp64" else 1e-9
+    for i in range(4):
+        x, y = i % 2, i // 2
+        assert abs(c.measure1(i, sz) - (0.5 if (x + y) % 2 == 0 else -0.5)) < tol
+    for (i, dx, dy) in I.SQUARE_2X2_BONDS:
+        assert abs(c.measure2(i, dx, dy, I.heisenberg_bond(2)) + 0.25) < tol
+    c.close()
+
+
 # Converged, well-posed cases (sigma_chi / sigma_0 of M >= 3e-7, the oracle
 # converges to < 1e-12): N = chi D^2 = 81, 32, 90 cut across the 64-wide
 # GEMM tiles; d > D in the second.  Cases whose chi reaches the noise floor
