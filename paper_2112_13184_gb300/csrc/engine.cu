@@ -448,35 +448,45 @@ ctm_status corner_core(ctm_ctx* h, const double* X1, const double* Tp, const dou
                        const double* Alu, double* out, bool open) {
     const int chi = h->chi, D = h->D, d = h->d, N = h->N;
     const int D2 = D * D;
-    // X2[(a,l,l'), (u,u',b)] = Tp[(a,l,l'), g] X1[g, (u,u',b)]
     const char* outer = h->tag;
     const std::string t2 = std::string(outer) + ".X2", t3 = std::string(outer) + ".X3",
                       t4 = std::string(outer) + ".X4";
-    {
-        ProfTag tg(h, t2.c_str());
-        CKS(gemm(h, false, false, N, N, chi, Tp, chi, X1, N, h->S1, N));
-    }
     if (h->opt.precision == CTM_OZAKI_BF16 && !open) {
-        // The same contraction with every permutation folded into the operand
-        // views of the tensor-core products and into the output layout.
-        const long long c = chi, Dl = D, dD2 = (long long)d * D2, M3 = c * c * D2;
-        // X3[(a,l',u',b), (s,r,d)] = X2[a,l,l',u,u',b] over (l,u) with Alu[(l,u),(s,r,d)]
-        const OzView x2r{4, {chi, D, D, chi}, {Dl * Dl * Dl * Dl * c, Dl * Dl * c, c, 1}};
-        const OzView x2k{2, {D, D, 1, 1}, {Dl * Dl * Dl * c, Dl * c, 0, 0}};
-        const OzView alu_n{1, {(int)dD2, 1, 1, 1}, {1, 0, 0, 0}}, alu_k{1, {D2, 1, 1, 1}, {dD2, 0, 0, 0}};
-        const OzView x3r{1, {(int)M3, 1, 1, 1}, {dD2, 0, 0, 0}}, x3c{1, {(int)dD2, 1, 1, 1}, {1, 0, 0, 0}};
+        // Tensor-core path.  Every permutation is folded into operand views and
+        // output layouts, chosen so that both large intermediates are plain
+        // K-contiguous row matrices (single-pass slicing) and the epilogue
+        // writes of X2 and X3 run along contiguous memory:
+        //   S1[a][b][l'][u'][l][u] = X2,  S2[a][b][r][d][s][l'][u'] = X3.
+        const long long c = chi, Dl = D, dD2 = (long long)d * D2, D4 = (long long)D2 * D2, M3 = c * c * D2;
         {
+            // X2^T[(b,u',u), (a,l,l')] = sum_g X1[g,u,u',b] Tp[a,l,l',g]
+            ProfTag tg(h, t2.c_str());
+            const OzView x1r{3, {chi, D, D, 1}, {1, c, Dl * c, 0}}, x1k{1, {chi, 1, 1, 1}, {N, 0, 0, 0}};
+            const OzView tpn{1, {N, 1, 1, 1}, {c, 0, 0, 0}}, tpk{1, {chi, 1, 1, 1}, {1, 0, 0, 0}};
+            const OzView s1r{3, {chi, D, D, 1}, {D4, D2, 1, 0}}, s1c{3, {chi, D, D, 1}, {c * D4, Dl, Dl * D2, 0}};
+            CKS(gemm_v(h, N, N, chi, X1, x1r, x1k, Tp, tpn, tpk, h->S1, s1r, s1c));
+        }
+        {
+            // X3[(a,b,l',u'), (s,r,d)] = S1[(a,b,l',u'), (l,u)] Alu[(l,u), (s,r,d)]
             ProfTag tg(h, t3.c_str());
+            const OzView x2r{1, {(int)M3, 1, 1, 1}, {D2, 0, 0, 0}}, x2k{1, {D2, 1, 1, 1}, {1, 0, 0, 0}};
+            const OzView alu_n{1, {(int)dD2, 1, 1, 1}, {1, 0, 0, 0}}, alu_k{1, {D2, 1, 1, 1}, {dD2, 0, 0, 0}};
+            const OzView x3r{3, {chi * chi, D, D, 1}, {D2 * dD2, Dl, 1, 0}};
+            const OzView x3c{3, {d, D, D, 1}, {D2, Dl * dD2, dD2, 0}};
             CKS(gemm_v(h, (int)M3, (int)dD2, D2, h->S1, x2r, x2k, Alu, alu_n, alu_k, h->S2, x3r, x3c));
         }
-        // Q[(a,d,d'), (b,r,r')] = X3[a,l',u',b,s,r,d] over (s,l',u') with A[(s,l',u'),(r',d')]
-        const OzView s2r{4, {chi, chi, D, D}, {Dl * c * dD2 * Dl, dD2, Dl, 1}};
-        const OzView s2k{3, {d, D, D, 1}, {D2, Dl * c * dD2, c * dD2, 0}};
+        // E[(a,d,d'), (b,r,r')] = S2[(a,b,r,d), (s,l',u')] A[(s,l',u'), (r',d')]
+        const OzView s2r{1, {(int)M3, 1, 1, 1}, {dD2, 0, 0, 0}}, s2k{1, {(int)dD2, 1, 1, 1}, {1, 0, 0, 0}};
         const OzView a_n{1, {D2, 1, 1, 1}, {1, 0, 0, 0}}, a_k{1, {(int)dD2, 1, 1, 1}, {D2, 0, 0, 0}};
         const OzView qr{4, {chi, chi, D, D}, {(long long)D2 * N, D2, Dl, Dl * N}};
         const OzView qc{2, {D, D, 1, 1}, {1, N, 0, 0}};
         ProfTag tg(h, t4.c_str());
         return gemm_v(h, (int)M3, D2, (int)dD2, h->S2, s2r, s2k, A, a_n, a_k, out, qr, qc);
+    }
+    // X2[(a,l,l'), (u,u',b)] = Tp[(a,l,l'), g] X1[g, (u,u',b)]
+    {
+        ProfTag tg(h, t2.c_str());
+        CKS(gemm(h, false, false, N, N, chi, Tp, chi, X1, N, h->S1, N));
     }
     // -> [a,l',u',b,l,u]
     CKS(perm(h, h->S1, h->S2, {chi, D, D, D, D, chi}, {0, 2, 4, 5, 1, 3}));

@@ -412,9 +412,9 @@ __global__ void __launch_bounds__(256) k_split_rows_reg(const double* __restrict
     }
 }
 
-// Rows contiguous (row stride 1), K at stride cs: lane = row, sixteen
+// Rows contiguous (row stride 1), K at stride cs: lane = row, 32
 // consecutive k per step (each load instruction reads 32 consecutive rows),
-// one warp per 32 rows x kspan k (kspan a multiple of 16); row maxima from
+// one warp per 32 rows x kspan k (kspan a multiple of 32); row maxima from
 // k_rowmax_cols.
 __global__ void __launch_bounds__(128) k_split_cols_reg(const double* __restrict__ X, int R, int K, int K8,
                                                        long long cs, int s,
@@ -430,16 +430,17 @@ __global__ void __launch_bounds__(128) k_split_cols_reg(const double* __restrict
     if (live && kg == 0) ex[r] = e;
     const size_t plane = (size_t)R * K8;
     const int kend = min(K8, (kg + 1) * kspan);
-    // 16 k per step: each lane then writes whole 32-byte sectors of every
-    // slice row (two 16-byte stores back to back), never half sectors that
-    // L2 would have to merge with a read from DRAM
-    for (int k0 = kg * kspan; k0 < kend; k0 += 16) {
-        double v[16];
+    // 32 k per step: each lane writes 64 contiguous bytes of every slice row
+    // (four 16-byte stores back to back).  Shorter runs per row left partly
+    // written lines that DRAM had to merge: 1.5x the bytes each way.
+    for (int k0 = kg * kspan; k0 < kend; k0 += 32) {
+        double v[32];
 #pragma unroll
-        for (int u = 0; u < 16; ++u) v[u] = (live && k0 + u < K) ? __ldcs(X + (long long)(k0 + u) * cs + r) : 0.0;
+        for (int u = 0; u < 32; ++u) v[u] = (live && k0 + u < K) ? __ldcs(X + (long long)(k0 + u) * cs + r) : 0.0;
         if (live) {
-            slice8_store(v, e, s, out + (size_t)r * K8 + k0, plane);
-            if (k0 + 8 < kend) slice8_store(v + 8, e, s, out + (size_t)r * K8 + k0 + 8, plane);
+#pragma unroll
+            for (int q = 0; q < 4; ++q)
+                if (k0 + 8 * q < kend) slice8_store(v + 8 * q, e, s, out + (size_t)r * K8 + k0 + 8 * q, plane);
         }
     }
 }
@@ -555,6 +556,7 @@ struct GemmArgs {
     int* PS1;
     float* PF;
     int Mpad, Npad;
+    int m_tiles, n_tiles;
     int* err;
 };
 
@@ -577,8 +579,16 @@ __global__ void __launch_bounds__(THREADS, 1)
     uint32_t* tmem_slot = (uint32_t*)(drain + 1);
 
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    const int m0 = blockIdx.x * BM, n0 = blockIdx.y * BN;
-    const int kb0 = blockIdx.z * g.kb_per_split;
+    // Direct output: a persistent grid strides over the m_tiles x n_tiles
+    // tiles, n fastest (CTAs running together share A tiles through L2), and
+    // the stage ring and the accumulator hand-off run on across tiles, so one
+    // tile's epilogue overlaps the next tile's loads and MMAs.  Split-K
+    // partials: one tile per CTA (blockIdx x: m, y: n, z: split).
+    const int ntiles = g.direct ? g.m_tiles * g.n_tiles : 1;
+    const int t_first = g.direct ? (int)blockIdx.x : 0, t_step = g.direct ? (int)gridDim.x : 1;
+    auto tile_m0 = [&](int t) { return (g.direct ? t / g.n_tiles : (int)blockIdx.x) * BM; };
+    auto tile_n0 = [&](int t) { return (g.direct ? t % g.n_tiles : (int)blockIdx.y) * BN; };
+    const int kb0 = g.direct ? 0 : (int)blockIdx.z * g.kb_per_split;
     const int kb1 = min(g.nkb, kb0 + g.kb_per_split);
     const int nkb = kb1 - kb0;
     const int nchunks = (nkb + CHUNK_KB - 1) / CHUNK_KB;
@@ -608,16 +618,23 @@ __global__ void __launch_bounds__(THREADS, 1)
         // ---------------- TMA producer ----------------
         if (lane == 0) {
             int issued = 0;
-            for (int i = 0; i < nkb; ++i) {
-                const int st = i % g.stages;
-                const uint32_t ph = (uint32_t)(i / g.stages) & 1u;
-                if (!mbar_wait(&empty[st], ph ^ 1u, g.err)) break;
-                uint8_t* sa = sbase + (size_t)st * g.stage_bytes;
-                mbar_expect_tx(&full[st], g.stage_bytes);
-                const int kc = (kb0 + i) * BK;
-                tma_load_3d(sa, &tmA, kc, m0, 0, &full[st]);
-                tma_load_3d(sa + g.a_bytes, &tmB, kc, n0, 0, &full[st]);
-                ++issued;
+            bool ok = true;
+            for (int t = t_first; t < ntiles && ok; t += t_step) {
+                const int m0 = tile_m0(t), n0 = tile_n0(t);
+                for (int i = 0; i < nkb; ++i) {
+                    const int st = issued % g.stages;
+                    const uint32_t ph = (uint32_t)(issued / g.stages) & 1u;
+                    if (!mbar_wait(&empty[st], ph ^ 1u, g.err)) {
+                        ok = false;
+                        break;
+                    }
+                    uint8_t* sa = sbase + (size_t)st * g.stage_bytes;
+                    mbar_expect_tx(&full[st], g.stage_bytes);
+                    const int kc = (kb0 + i) * BK;
+                    tma_load_3d(sa, &tmA, kc, m0, 0, &full[st]);
+                    tma_load_3d(sa + g.a_bytes, &tmB, kc, n0, 0, &full[st]);
+                    ++issued;
+                }
             }
             if (*(volatile int*)g.err) {
                 // let the copies still in flight land before the CTA exits
@@ -634,14 +651,22 @@ __global__ void __launch_bounds__(THREADS, 1)
         if (lane == 0) {
             const uint32_t idesc = (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(BN >> 3) << 17) |
                                    ((uint32_t)(BM >> 4) << 24);
-            for (int i = 0; i < nkb; ++i) {
-                const int st = i % g.stages;
-                const uint32_t ph = (uint32_t)(i / g.stages) & 1u;
-                const int chunk = i / CHUNK_KB;
+            int it = 0, cc = 0;  // k-blocks and accumulator chunks issued so far, over all tiles
+            bool ok = true;
+            for (int t = t_first; t < ntiles && ok; t += t_step)
+            for (int i = 0; i < nkb; ++i, ++it) {
+                const int st = it % g.stages;
+                const uint32_t ph = (uint32_t)(it / g.stages) & 1u;
                 const bool first = (i % CHUNK_KB) == 0;
                 const bool last = (i % CHUNK_KB) == CHUNK_KB - 1 || i == nkb - 1;
-                if (first && chunk > 0 && !mbar_wait(acc_empty, (uint32_t)(chunk - 1) & 1u, g.err)) break;
-                if (!mbar_wait(&full[st], ph, g.err)) break;
+                if (first && cc > 0 && !mbar_wait(acc_empty, (uint32_t)(cc - 1) & 1u, g.err)) {
+                    ok = false;
+                    break;
+                }
+                if (!mbar_wait(&full[st], ph, g.err)) {
+                    ok = false;
+                    break;
+                }
                 tc_fence_after();
                 const uint32_t sa = base + (uint32_t)st * g.stage_bytes;
                 const uint32_t sb = sa + g.a_bytes;
@@ -659,7 +684,10 @@ __global__ void __launch_bounds__(THREADS, 1)
                         }
                 }
                 tc_commit(&empty[st]);
-                if (last) tc_commit(acc_full);
+                if (last) {
+                    tc_commit(acc_full);
+                    ++cc;
+                }
             }
             // every MMA issued by this thread completes before TMEM is freed
             tc_commit(drain);
@@ -671,15 +699,18 @@ __global__ void __launch_bounds__(THREADS, 1)
         // ---------------- epilogue: warps 0..11 ----------------
         const int q = warp & 3, grp = warp >> 2;
         const uint32_t lane_addr = tmem + ((uint32_t)(q * 32) << 16);
+        int cc = 0;  // accumulator chunks drained so far, over all tiles
+        bool ok = true;
+        for (int t = t_first; t < ntiles && ok; t += t_step) {
+        const int m0 = tile_m0(t), n0 = tile_n0(t);
         int S0[NBG][16], S1[NBG][16];
         float F[NBG][16];
 #pragma unroll
         for (int jb = 0; jb < NBG; ++jb)
 #pragma unroll
             for (int j = 0; j < 16; ++j) S0[jb][j] = S1[jb][j] = 0, F[jb][j] = 0.f;
-        bool ok = true;
-        for (int c = 0; c < nchunks; ++c) {
-            if (!mbar_wait(acc_full, (uint32_t)c & 1u, g.err)) {
+        for (int c = 0; c < nchunks; ++c, ++cc) {
+            if (!mbar_wait(acc_full, (uint32_t)cc & 1u, g.err)) {
                 ok = false;
                 break;
             }
@@ -748,6 +779,7 @@ __global__ void __launch_bounds__(THREADS, 1)
                 }
             }
         }
+        }  // tiles
     }
     tc_fence_before();
     __syncthreads();
@@ -866,6 +898,15 @@ cudaError_t launch_gemm(const Plan& p, const CUtensorMap& ta, const CUtensorMap&
         attr = true;
     }
     dim3 grid(p.m_tiles, p.n_tiles, p.ksplit);
+    if (g.direct) {
+        // persistent: one CTA per SM (the stage ring fills shared memory)
+        int dev = 0, nsm = 0;
+        cudaError_t e = cudaGetDevice(&dev);
+        if (e == cudaSuccess) e = cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
+        if (e != cudaSuccess) return e;
+        const long long tiles = (long long)p.m_tiles * p.n_tiles;
+        grid = dim3((unsigned)std::min<long long>(tiles, nsm > 0 ? nsm : 1), 1, 1);
+    }
     ++g_launches;
     oz::k_oz_gemm<NB16><<<grid, oz::THREADS, p.smem, st>>>(ta, tb, g);
     return cudaGetLastError();
@@ -1009,6 +1050,8 @@ cudaError_t oz_gemm_view(int M, int N, int K, int s, const void* Asplit, const v
         g.out_c.stride[a] = ocv.stride[a];
     }
     g.Mpad = p.m_tiles * oz::BM;
+    g.m_tiles = p.m_tiles;
+    g.n_tiles = p.n_tiles;
     g.Npad = p.n_tiles * p.bn;
     if (!g.direct) {
         const size_t part = align256((size_t)p.ksplit * g.Mpad * g.Npad * 4);
