@@ -150,6 +150,48 @@ def run_reference(args):
     print(json.dumps(line), flush=True)
 
 
+def oz_gemm_roofline(by_op):
+    """Roofline of the emulated-FP64 GEMM class (k_oz_gemm) over one sweep.
+
+    Each operation tag records its tensor flops (2 M N K per BF16 slice
+    product, s(s+1)/2 products) and algorithmic bytes (BF16 slices of both
+    operands + FP64 output).  Per tag the roofline time is
+    max(F / P_tensor, B / BW); the class is reported in the unit of the
+    bound that dominates its summed roofline time, with the roofline-time
+    fraction (sum of roofline times / measured time) beside it."""
+    peaks = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
+    tc = peaks["bf16_tflops_sustained"] * 1e12
+    bw = peaks["hbm_gbs"] * 1e9
+    F = B = T = t_tc = t_bw = t_roof = 0.0
+    ops = {}
+    for tag, v in by_op.items():
+        if not tag.endswith("/gemm") or v["ms"] <= 0:
+            continue
+        f, b, t = v["flops"], v["bytes"], v["ms"] / 1e3
+        tr = max(f / tc, b / bw)
+        F, B, T = F + f, B + b, T + t
+        t_tc, t_bw, t_roof = t_tc + f / tc, t_bw + b / bw, t_roof + tr
+        ops[tag] = {"ms": round(v["ms"], 3), "bound": "tensor" if f / tc >= b / bw else "hbm",
+                    "roofline_frac": round(tr / t, 4)}
+    if T <= 0:
+        return None
+    tensor = t_tc >= t_bw
+    achieved = F / T / 1e12 if tensor else B / T / 1e9
+    peak = tc / 1e12 if tensor else bw / 1e9
+    top = dict(sorted(ops.items(), key=lambda kv: -kv[1]["ms"])[:8])
+    return {"bound": "tensor" if tensor else "hbm", "kernel": "k_oz_gemm (tcgen05 BF16 slice products)",
+            "achieved": achieved, "peak": peak, "unit": "TFLOP/s" if tensor else "GB/s",
+            "frac": achieved / peak, "traffic": None,
+            "peak_source": ("MEASURED_PEAKS.json bf16_tflops_sustained (of measured)" if tensor
+                            else "MEASURED_PEAKS.json hbm_gbs (of measured)"),
+            "roofline_time_frac": t_roof / T, "class_ms": T * 1e3,
+            "note": ("achieved = sum over the sweep's emulated GEMMs of the algorithmic work in the "
+                     "bound's unit / their summed device time; roofline_time_frac = "
+                     "sum max(F/P_tensor, B/BW) / measured time (shapes range from tensor- to "
+                     "HBM-bound); traffic: per-shape DRAM bytes are in profiles/"),
+            "ops": top}
+
+
 # ---------------------------------------------------------------------------
 # our arm
 # ---------------------------------------------------------------------------
@@ -182,10 +224,12 @@ def run_ours(args):
     barrier()
     ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     with ClockSampler(local) as clk:
+        torch.cuda.nvtx.range_push("timed")  # lets a profiler keep to the timed sweeps
         ev0.record(stream)
         solver.sweep(args.steps)
         ev1.record(stream)
         barrier()
+        torch.cuda.nvtx.range_pop()
     ms = ev0.elapsed_time(ev1)
     # kernels launched per sweep: counted on one eager, event-timed sweep
     # (graph replays launch the same kernels without host calls); the same
@@ -241,12 +285,7 @@ def run_ours(args):
                     "frac": achieved / FP64_NOMINAL_TFLOPS if achieved else None, "traffic": None,
                     "peak_source": "GB300 FP64 nominal 1.25 TFLOP/s (profiling recipe table)"}
         else:
-            peaks = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
-            pk = peaks["bf16_tflops_sustained"]
-            roof = {"bound": "tensor", "kernel": "k_oz_gemm (tcgen05 BF16 slice products)", "achieved": achieved,
-                    "peak": pk,
-                    "unit": "TFLOP/s", "frac": achieved / pk if achieved else None, "traffic": None,
-                    "peak_source": "MEASURED_PEAKS.json bf16_tflops_sustained (of measured)"}
+            roof = oz_gemm_roofline(by_op)
         total_ms = sum(p["ms"] for p in prof.values())
         line = {
             "metric": METRIC, "value": value, "unit": "sweeps/s", "n_gpus": world, "steps": args.steps,
@@ -263,8 +302,8 @@ def run_ours(args):
             "gpu_launches": launches,
             "clocks": clk.summary(),
             "profile_note": prof_note,
-            "profile_by_op": {k: {"ms": round(v["ms"], 3), "calls": v["calls"]} for k, v in
-                              sorted(by_op.items(), key=lambda kv: -kv[1]["ms"])},
+            "profile_by_op": {k: {"ms": round(v["ms"], 3), "calls": v["calls"], "launches": v.get("launches")}
+                              for k, v in sorted(by_op.items(), key=lambda kv: -kv[1]["ms"])},
             "profile": {k: {"ms": round(v["ms"], 3), "share": round(v["ms"] / total_ms, 4) if total_ms else None,
                             "calls": v["calls"], "tflops": (v["flops"] / (v["ms"] / 1e3) / 1e12)
                             if v["ms"] > 0 and v["flops"] > 0 else None}

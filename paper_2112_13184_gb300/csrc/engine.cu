@@ -107,10 +107,11 @@ struct ctm_ctx {
     bool prof = false;
     std::vector<cudaEvent_t> ev_pool;
     size_t ev_used = 0;
-    struct Rec { int cls; size_t ev; double flops, bytes; const char* tag; };
+    std::vector<long long> ev_launch0;  // kernel-launch count at each record's start
+    struct Rec { int cls; size_t ev; double flops, bytes; const char* tag; long long launches; };
     std::vector<Rec> recs;
     const char* tag = "other";  // label of the calls being issued (ProfTag)
-    struct TagAcc { double ms = 0, flops = 0, bytes = 0; long long calls = 0; };
+    struct TagAcc { double ms = 0, flops = 0, bytes = 0; long long calls = 0, launches = 0; };
     std::map<std::string, TagAcc> tags;
     double p_ms[8] = {}, p_flops[8] = {}, p_bytes[8] = {};
     long long p_calls[8] = {};
@@ -245,13 +246,15 @@ size_t prof_begin(ctm_ctx* h) {
     }
     const size_t i = h->ev_used;
     cudaEventRecord(h->ev_pool[i], h->stream);
+    if (h->ev_launch0.size() < h->ev_pool.size()) h->ev_launch0.resize(h->ev_pool.size());
+    h->ev_launch0[i] = ctm::g_launches;
     h->ev_used += 2;
     return i;
 }
 void prof_end(ctm_ctx* h, size_t i, int cls, double flops, double bytes) {
     if (i == NO_EV) return;
     cudaEventRecord(h->ev_pool[i + 1], h->stream);
-    h->recs.push_back({cls, i, flops, bytes, h->tag});
+    h->recs.push_back({cls, i, flops, bytes, h->tag, ctm::g_launches - h->ev_launch0[i]});
 }
 
 // labels every profiled call issued in its scope (nested scopes restore)
@@ -280,6 +283,7 @@ void prof_collect(ctm_ctx* h) {
         t.flops += r.flops;
         t.bytes += r.bytes;
         t.calls += 1;
+        t.launches += r.launches;
     }
     h->recs.clear();
     h->ev_used = 0;
@@ -288,6 +292,15 @@ void prof_collect(ctm_ctx* h) {
 // ----------------------------------------------------------------------------
 // contractions
 // ----------------------------------------------------------------------------
+// Emulated FP64 product on the tensor cores: s(s+1)/2 BF16 slice products
+// of 2 M N K flops each (levels 0..s-1, level L holding L+1 products); its
+// algorithmic bytes are the BF16 slices of both operands (K padded to 8) and
+// the FP64 output (read too when beta != 0).
+double oz_flops(int M, int N, int K, int s) { return 2.0 * M * N * K * (s * (s + 1) / 2); }
+double oz_bytes(int M, int N, int K, int s, bool beta) {
+    const double K8 = (double)((K + 7) & ~7);
+    return 2.0 * s * ((double)M * K8 + (double)N * K8) + 8.0 * M * N * (beta ? 2.0 : 1.0);
+}
 void slices_written(ctm_ctx* h, const double* p) {
     for (auto& c : h->ozc)
         if (c.ptr == p) c.valid = false;
@@ -328,7 +341,7 @@ ctm_status gemm(ctm_ctx* h, bool tA, bool tB, int M, int N, int K, const double*
         CKS(split_(h, B, N, K, tB ? ldb : 1, tB ? 1 : ldb, h->ozB));
         const size_t ev = prof_begin(h);
         CK(ctm::oz_gemm(M, N, K, s, sa, h->ozB, 1.0, beta, C, ldc, h->ozW, h->ozW_n, h->flag + 1, h->stream));
-        prof_end(h, ev, P_GEMM, flops, bytes);
+        prof_end(h, ev, P_GEMM, oz_flops(M, N, K, s), oz_bytes(M, N, K, s, beta != 0.0));
     } else {
         const size_t ev = prof_begin(h);
         CK(ctm::dgemm(tA, tB, M, N, K, 1.0, A, lda, B, ldb, beta, C, ldc, h->stream, h->splitk, h->splitk_n));
@@ -358,7 +371,7 @@ ctm_status gemm_v(ctm_ctx* h, int M, int N, int K, const double* A, const OzView
     ev = prof_begin(h);
     CK(ctm::oz_gemm_view(M, N, K, s, h->ozA, h->ozB, 1.0, 0.0, C, cr, cc, h->ozW, h->ozW_n, h->flag + 1,
                          h->stream));
-    prof_end(h, ev, P_GEMM, 2.0 * M * N * K, 8.0 * ((double)M * K + (double)K * N + (double)M * N));
+    prof_end(h, ev, P_GEMM, oz_flops(M, N, K, s), oz_bytes(M, N, K, s, false));
     return CTM_OK;
 }
 
@@ -1207,9 +1220,10 @@ ctm_status ctm_profile_report(ctm_handle h, char* buf, size_t len, int reset) {
     bool first = true;
     char tmp[256];
     for (const auto& kv : h->tags) {
-        snprintf(tmp, sizeof(tmp), "%s\"%s\": {\"ms\": %.4f, \"calls\": %lld, \"flops\": %.6g, \"bytes\": %.6g}",
-                 first ? "" : ", ", kv.first.c_str(), kv.second.ms, kv.second.calls, kv.second.flops,
-                 kv.second.bytes);
+        snprintf(tmp, sizeof(tmp),
+                 "%s\"%s\": {\"ms\": %.4f, \"calls\": %lld, \"launches\": %lld, \"flops\": %.6g, \"bytes\": %.6g}",
+                 first ? "" : ", ", kv.first.c_str(), kv.second.ms, kv.second.calls, kv.second.launches,
+                 kv.second.flops, kv.second.bytes);
         out += tmp;
         first = false;
     }

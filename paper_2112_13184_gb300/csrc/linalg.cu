@@ -173,16 +173,36 @@ __device__ __forceinline__ void cluster_sync() {
     asm volatile("barrier.cluster.arrive.release.aligned;\n\tbarrier.cluster.wait.acquire.aligned;" ::: "memory");
 }
 
+// Per pair only the cross product g_p.g_q is formed: the squared column
+// norms are tracked (a <- a - t c, b <- b + t c for the rotation with t =
+// tan(theta)) and recomputed exactly at the start of every sweep; for k <=
+// 256 the pair's columns stay in registers between the product and the
+// rotation.
 __global__ void __launch_bounds__(256) k_jacobi_cluster(double* __restrict__ Gt, double* __restrict__ Wt, int k,
                                                        int n, int max_sweeps, double tol,
-                                                       unsigned long long* __restrict__ off, int csize) {
+                                                       unsigned long long* __restrict__ off,
+                                                       double* __restrict__ nrm, int csize) {
+    constexpr int RK = 8;  // cached entries per lane: k <= 32 RK
     const int b = blockIdx.x / csize, rank = blockIdx.x % csize;
     const int warps = blockDim.x >> 5, lane = threadIdx.x & 31;
     const int gw = rank * warps + (threadIdx.x >> 5), nw = csize * warps;
     double* g = Gt + (size_t)b * k * k;
     double* wm = Wt ? Wt + (size_t)b * k * k : nullptr;
+    double* nb2 = nrm + (size_t)b * k;
     unsigned long long* offb = off + (size_t)b * max_sweeps;
+    const bool cached = k <= 32 * RK;
     for (int sw = 0; sw < max_sweeps; ++sw) {
+        for (int c = gw; c < k; c += nw) {
+            const double* gc = g + (size_t)c * k;
+            double a = 0.0;
+            for (int i = lane; i < k; i += 32) {
+                const double x = __ldcg(gc + i);
+                a = fma(x, x, a);
+            }
+            for (int o = 16; o > 0; o >>= 1) a += __shfl_xor_sync(0xffffffffu, a, o);
+            if (lane == 0) __stcg(nb2 + c, a);
+        }
+        cluster_sync();
         for (int r = 0; r < n - 1; ++r) {
             for (int p = gw; p < n / 2; p += nw) {
                 auto pos = [&](int i) { return i == 0 ? 0 : 1 + (i - 1 + r) % (n - 1); };
@@ -191,18 +211,21 @@ __global__ void __launch_bounds__(256) k_jacobi_cluster(double* __restrict__ Gt,
                 if (P > Q) { const int t = P; P = Q; Q = t; }
                 double* gp = g + (size_t)P * k;
                 double* gq = g + (size_t)Q * k;
-                double a = 0.0, bb = 0.0, c = 0.0;
-                for (int i = lane; i < k; i += 32) {
-                    const double x = __ldcg(gp + i), y = __ldcg(gq + i);
-                    a = fma(x, x, a);
-                    bb = fma(y, y, bb);
-                    c = fma(x, y, c);
+                double xr[RK], yr[RK];
+                double c = 0.0;
+                if (cached) {
+#pragma unroll
+                    for (int u = 0; u < RK; ++u) {
+                        const int i = lane + 32 * u;
+                        xr[u] = i < k ? __ldcg(gp + i) : 0.0;
+                        yr[u] = i < k ? __ldcg(gq + i) : 0.0;
+                        c = fma(xr[u], yr[u], c);
+                    }
+                } else {
+                    for (int i = lane; i < k; i += 32) c = fma(__ldcg(gp + i), __ldcg(gq + i), c);
                 }
-                for (int o = 16; o > 0; o >>= 1) {
-                    a += __shfl_xor_sync(0xffffffffu, a, o);
-                    bb += __shfl_xor_sync(0xffffffffu, bb, o);
-                    c += __shfl_xor_sync(0xffffffffu, c, o);
-                }
+                for (int o = 16; o > 0; o >>= 1) c += __shfl_xor_sync(0xffffffffu, c, o);
+                const double a = __ldcg(nb2 + P), bb = __ldcg(nb2 + Q);
                 if (a < 1e-280 || bb < 1e-280) continue;  // zero or near underflow: nothing to rotate
                 const double rel = fabs(c) / (sqrt(a) * sqrt(bb));
                 if (lane == 0) atomicMax(offb + sw, (unsigned long long)__double_as_longlong(rel));
@@ -210,10 +233,25 @@ __global__ void __launch_bounds__(256) k_jacobi_cluster(double* __restrict__ Gt,
                 const double z = (bb - a) / (2.0 * c);
                 const double t = (z >= 0.0 ? 1.0 : -1.0) / (fabs(z) + sqrt(1.0 + z * z));
                 const double cs = 1.0 / sqrt(1.0 + t * t), sn = cs * t;
-                for (int i = lane; i < k; i += 32) {
-                    const double x = __ldcg(gp + i), y = __ldcg(gq + i);
-                    __stcg(gp + i, cs * x - sn * y);
-                    __stcg(gq + i, sn * x + cs * y);
+                if (cached) {
+#pragma unroll
+                    for (int u = 0; u < RK; ++u) {
+                        const int i = lane + 32 * u;
+                        if (i < k) {
+                            __stcg(gp + i, cs * xr[u] - sn * yr[u]);
+                            __stcg(gq + i, sn * xr[u] + cs * yr[u]);
+                        }
+                    }
+                } else {
+                    for (int i = lane; i < k; i += 32) {
+                        const double x = __ldcg(gp + i), y = __ldcg(gq + i);
+                        __stcg(gp + i, cs * x - sn * y);
+                        __stcg(gq + i, sn * x + cs * y);
+                    }
+                }
+                if (lane == 0) {
+                    __stcg(nb2 + P, a - t * c);
+                    __stcg(nb2 + Q, bb + t * c);
                 }
                 if (wm) {
                     double* wp = wm + (size_t)P * k;
@@ -532,7 +570,8 @@ cudaError_t qr(const double* Y, int N, int k, double* Q, double* R, void* ws, cu
 
 // Jacobi on nb matrices: one 16-CTA cluster per matrix when the device
 // allows it (8 otherwise), else one launch per round.
-cudaError_t jacobi(double* Gt, double* Wt, int k, int n, int nb, unsigned long long* off, cudaStream_t s) {
+cudaError_t jacobi(double* Gt, double* Wt, int k, int n, int nb, unsigned long long* off, double* nrm,
+                   cudaStream_t s) {
     static int csize = -1;
     if (csize < 0) {
         csize = 0;
@@ -557,7 +596,7 @@ cudaError_t jacobi(double* Gt, double* Wt, int k, int n, int nb, unsigned long l
         cfg.numAttrs = 1;
         ++g_launches;
         const cudaError_t e = cudaLaunchKernelEx(&cfg, k_jacobi_cluster, Gt, Wt, k, n, JACOBI_MAX_SWEEPS,
-                                                 jacobi_tol(k), off, csize);
+                                                 jacobi_tol(k), off, nrm, csize);
         if (e == cudaSuccess) return cudaSuccess;
         cudaGetLastError();
         --g_launches;
@@ -571,15 +610,18 @@ cudaError_t jacobi(double* Gt, double* Wt, int k, int n, int nb, unsigned long l
     return cudaGetLastError();
 }
 
+// scratch: G^T and W^T (k x k each), squared column norms (k), per-sweep
+// off-diagonal maxima
 size_t svd_ws_bytes(int k) {
-    return sizeof(double) * 2 * (size_t)k * k + sizeof(unsigned long long) * JACOBI_MAX_SWEEPS + 256;
+    return sizeof(double) * (2 * (size_t)k * k + k) + sizeof(unsigned long long) * JACOBI_MAX_SWEEPS + 256;
 }
 
 cudaError_t svd(const double* G, int k, double* U, double* S, double* V, void* ws, cudaStream_t s) {
     if (k <= 0 || k > 1024) return cudaErrorInvalidValue;
     double* Gt = (double*)ws;
     double* Wt = Gt + (size_t)k * k;
-    unsigned long long* off = (unsigned long long*)(Wt + (size_t)k * k);
+    double* nrm = Wt + (size_t)k * k;
+    unsigned long long* off = (unsigned long long*)(nrm + k);
     cudaError_t e = cudaMemsetAsync(off, 0, sizeof(unsigned long long) * JACOBI_MAX_SWEEPS, s);
     if (e) return e;
     ++g_launches;
@@ -587,7 +629,7 @@ cudaError_t svd(const double* G, int k, double* U, double* S, double* V, void* w
     ++g_launches;
     k_eye_batch<<<grid_for((size_t)k * k), 256, 0, s>>>(Wt, k, 1);
     const int n = k + (k & 1);
-    e = jacobi(Gt, Wt, k, n, 1, off, s);
+    e = jacobi(Gt, Wt, k, n, 1, off, nrm, s);
     if (e) return e;
     ++g_launches;
     k_jacobi_finish<<<1, 256, sizeof(double) * k, s>>>(Gt, Wt, k, U, S, V);
@@ -595,19 +637,21 @@ cudaError_t svd(const double* G, int k, double* U, double* S, double* V, void* w
 }
 
 size_t svals_ws_bytes(int k, int nb) {
-    return sizeof(double) * (size_t)nb * k * k + sizeof(unsigned long long) * JACOBI_MAX_SWEEPS * nb + 256;
+    return sizeof(double) * (size_t)nb * ((size_t)k * k + k) + sizeof(unsigned long long) * JACOBI_MAX_SWEEPS * nb +
+           256;
 }
 
 cudaError_t svals_normalised(const double* Gs, int k, int nb, double* out, void* ws, cudaStream_t s) {
     if (k <= 0 || k > 1024 || nb <= 0 || nb > 65535) return cudaErrorInvalidValue;
     double* Gt = (double*)ws;
-    unsigned long long* off = (unsigned long long*)(Gt + (size_t)nb * k * k);
+    double* nrm = Gt + (size_t)nb * k * k;
+    unsigned long long* off = (unsigned long long*)(nrm + (size_t)nb * k);
     cudaError_t e = cudaMemsetAsync(off, 0, sizeof(unsigned long long) * JACOBI_MAX_SWEEPS * nb, s);
     if (e) return e;
     ++g_launches;
     k_transpose_batch<<<grid_for((size_t)nb * k * k), 256, 0, s>>>(Gs, Gt, k, nb);
     const int n = k + (k & 1);
-    e = jacobi(Gt, nullptr, k, n, nb, off, s);
+    e = jacobi(Gt, nullptr, k, n, nb, off, nrm, s);
     if (e) return e;
     ++g_launches;
     k_svals_finish<<<nb, 256, sizeof(double) * k, s>>>(Gt, k, out);
@@ -624,7 +668,7 @@ cudaError_t svals_normalised(const double* Gs, int k, int nb, double* out, void*
 namespace {
 constexpr int SVD_NOALLOC_MAX_K = 256;
 constexpr size_t SVD_NOALLOC_BYTES =
-    sizeof(double) * 2 * (size_t)SVD_NOALLOC_MAX_K * SVD_NOALLOC_MAX_K +
+    sizeof(double) * (2 * (size_t)SVD_NOALLOC_MAX_K * SVD_NOALLOC_MAX_K + SVD_NOALLOC_MAX_K) +
     sizeof(unsigned long long) * JACOBI_MAX_SWEEPS + 256;
 static __device__ __align__(256) unsigned char g_svd_scratch[SVD_NOALLOC_BYTES];
 
@@ -637,8 +681,9 @@ int svd_noalloc_max_k() { return SVD_NOALLOC_MAX_K; }
 
 cudaError_t svd_noalloc(const double* G, int k, double* U, double* S, double* V, cudaStream_t s) {
     if (k <= 0 || k > SVD_NOALLOC_MAX_K) return cudaErrorInvalidValue;
-    static_assert(SVD_NOALLOC_BYTES >= sizeof(double) * 2 * (size_t)SVD_NOALLOC_MAX_K * SVD_NOALLOC_MAX_K +
-                                           sizeof(unsigned long long) * JACOBI_MAX_SWEEPS,
+    static_assert(SVD_NOALLOC_BYTES + 256 >= sizeof(double) * (2 * (size_t)SVD_NOALLOC_MAX_K * SVD_NOALLOC_MAX_K +
+                                                               SVD_NOALLOC_MAX_K) +
+                                                sizeof(unsigned long long) * JACOBI_MAX_SWEEPS + 256,
                   "scratch holds the Jacobi workspace of the largest k");
     int dev = 0;
     cudaError_t e = cudaGetDevice(&dev);

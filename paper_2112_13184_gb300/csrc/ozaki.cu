@@ -334,7 +334,8 @@ __device__ __forceinline__ unsigned bf2_bits(float a, float b) {
     const __nv_bfloat162 p = __floats2bfloat162_rn(a, b);  // a in the low half (lower address)
     return *reinterpret_cast<const unsigned*>(&p);
 }
-__device__ __forceinline__ void slice8_store(const double* v, int e, int s, __nv_bfloat16* dst, size_t plane) {
+// slice t of eight consecutive values as 8 BF16 (16 bytes), t < s
+__device__ __forceinline__ void slice8_pack(const double* v, int e, int s, uint4* q) {
     int d[8][MAX_S];
 #pragma unroll
     for (int u = 0; u < 8; ++u) digits(v[u], e, s, d[u]);
@@ -342,14 +343,19 @@ __device__ __forceinline__ void slice8_store(const double* v, int e, int s, __nv
     for (int t = 0; t < MAX_S; ++t) {
         if (t < s) {
             const float sc = __int_as_float((127 - 8 * t) << 23);  // 2^(-8t)
-            uint4 q;
-            q.x = bf2_bits((float)d[0][t] * sc, (float)d[1][t] * sc);
-            q.y = bf2_bits((float)d[2][t] * sc, (float)d[3][t] * sc);
-            q.z = bf2_bits((float)d[4][t] * sc, (float)d[5][t] * sc);
-            q.w = bf2_bits((float)d[6][t] * sc, (float)d[7][t] * sc);
-            *reinterpret_cast<uint4*>(dst + t * plane) = q;
+            q[t].x = bf2_bits((float)d[0][t] * sc, (float)d[1][t] * sc);
+            q[t].y = bf2_bits((float)d[2][t] * sc, (float)d[3][t] * sc);
+            q[t].z = bf2_bits((float)d[4][t] * sc, (float)d[5][t] * sc);
+            q[t].w = bf2_bits((float)d[6][t] * sc, (float)d[7][t] * sc);
         }
     }
+}
+__device__ __forceinline__ void slice8_store(const double* v, int e, int s, __nv_bfloat16* dst, size_t plane) {
+    uint4 q[MAX_S];
+    slice8_pack(v, e, s, q);
+#pragma unroll
+    for (int t = 0; t < MAX_S; ++t)
+        if (t < s) *reinterpret_cast<uint4*>(dst + t * plane) = q[t];
 }
 
 // K contiguous, rows at stride rs, K8 <= 4 * 8 * TPR: TPR threads per row,
@@ -415,33 +421,50 @@ __global__ void __launch_bounds__(256) k_split_rows_reg(const double* __restrict
 // Rows contiguous (row stride 1), K at stride cs: lane = row, 32
 // consecutive k per step (each load instruction reads 32 consecutive rows),
 // one warp per 32 rows x kspan k (kspan a multiple of 32); row maxima from
-// k_rowmax_cols.
-__global__ void __launch_bounds__(128) k_split_cols_reg(const double* __restrict__ X, int R, int K, int K8,
-                                                       long long cs, int s,
-                                                       const unsigned long long* __restrict__ maxbits,
-                                                       __nv_bfloat16* __restrict__ out, int* __restrict__ ex,
-                                                       int kspan, int kgroups) {
+// k_rowmax_cols.  The slices go out through shared memory so that four lanes
+// write one row's 64 contiguous bytes in the same store instruction: lanes
+// that each wrote 16 bytes of a different row left half-written sectors
+// that L2 filled from DRAM (1.5x the bytes each way).
+__global__ void __launch_bounds__(64) k_split_cols_reg(const double* __restrict__ X, int R, int K, int K8,
+                                                      long long cs, int s,
+                                                      const unsigned long long* __restrict__ maxbits,
+                                                      __nv_bfloat16* __restrict__ out, int* __restrict__ ex,
+                                                      int kspan, int kgroups) {
+    // per warp: every slice of 32 rows x 4 x 16 bytes (+1 pad against bank conflicts)
+    __shared__ uint4 tile[2][MAX_S][32][5];
     const int wid = (int)((blockIdx.x * (size_t)blockDim.x + threadIdx.x) >> 5), lane = threadIdx.x & 31;
+    const int w = threadIdx.x >> 5;
     const int rg = wid / kgroups, kg = wid - rg * kgroups;
     if (rg * 32 >= R) return;
-    const int r = rg * 32 + lane;
+    const int r0 = rg * 32, r = r0 + lane;
     const bool live = r < R;
     const int e = live ? row_exponent(__longlong_as_double((long long)maxbits[r])) : 0;
     if (live && kg == 0) ex[r] = e;
     const size_t plane = (size_t)R * K8;
     const int kend = min(K8, (kg + 1) * kspan);
-    // 32 k per step: each lane writes 64 contiguous bytes of every slice row
-    // (four 16-byte stores back to back).  Shorter runs per row left partly
-    // written lines that DRAM had to merge: 1.5x the bytes each way.
     for (int k0 = kg * kspan; k0 < kend; k0 += 32) {
         double v[32];
 #pragma unroll
         for (int u = 0; u < 32; ++u) v[u] = (live && k0 + u < K) ? __ldcs(X + (long long)(k0 + u) * cs + r) : 0.0;
-        if (live) {
 #pragma unroll
-            for (int q = 0; q < 4; ++q)
-                if (k0 + 8 * q < kend) slice8_store(v + 8 * q, e, s, out + (size_t)r * K8 + k0 + 8 * q, plane);
+        for (int c = 0; c < 4; ++c) {
+            uint4 q[MAX_S];
+            slice8_pack(v + 8 * c, e, s, q);
+#pragma unroll
+            for (int t = 0; t < MAX_S; ++t)
+                if (t < s) tile[w][t][lane][c] = q[t];
         }
+        __syncwarp();
+        // lane -> (row rr = j * 8 + lane / 4, 16-byte chunk c = lane % 4)
+        for (int t = 0; t < s; ++t)
+#pragma unroll
+            for (int j = 0; j < 4; ++j) {
+                const int rr = j * 8 + (lane >> 2), c = lane & 3;
+                if (r0 + rr < R && k0 + 8 * c < kend)
+                    *reinterpret_cast<uint4*>(out + t * plane + (size_t)(r0 + rr) * K8 + k0 + 8 * c) =
+                        tile[w][t][rr][c];
+            }
+        __syncwarp();
     }
 }
 
@@ -986,12 +1009,12 @@ cudaError_t oz_split_view(const double* X, int R, int K, const OzView& rvh, cons
         const unsigned long long warps = (unsigned long long)rg * kr;
         const int kspan = 256, kgroups = (K8 + kspan - 1) / kspan;
         const unsigned long long warps2 = (unsigned long long)rg * kgroups;
-        if ((warps + 3) / 4 > 0x7fffffffull || (warps2 + 3) / 4 > 0x7fffffffull) return cudaErrorInvalidValue;
+        if ((warps + 3) / 4 > 0x7fffffffull || (warps2 + 1) / 2 > 0x7fffffffull) return cudaErrorInvalidValue;
         ++g_launches;
         oz::k_rowmax_cols<<<(unsigned)((warps + 3) / 4), 128, 0, st>>>(X, R, K, rv, kv, (int)kr, mb);
         ++g_launches;
-        oz::k_split_cols_reg<<<(unsigned)((warps2 + 3) / 4), 128, 0, st>>>(X, R, K, K8, kv.stride[0], s, mb, sl, ex,
-                                                                            kspan, kgroups);
+        oz::k_split_cols_reg<<<(unsigned)((warps2 + 1) / 2), 64, 0, st>>>(X, R, K, K8, kv.stride[0], s, mb, sl, ex,
+                                                                           kspan, kgroups);
     } else {
         cudaError_t e = cudaMemsetAsync(mb, 0, (size_t)R * 8, st);
         if (e != cudaSuccess) return e;

@@ -80,7 +80,23 @@ def split_e():
     print("split_e done", float(Y[0, 0]))
 
 
-CASES = {"split_e": split_e, "apply_fp64": apply_fp64, "apply_oz": apply_oz, "x2_oz": x2_oz, "x3_oz": x3_oz, "x4t_oz": x4t_oz}
+def sweep_mixed_chi64():
+    """One emulated-FP64 sweep at d=3, D=8, chi=64 (N = 4096, corners 134 MB):
+    every kernel of the sweep in its real operand layouts (strided corner
+    views, slice caches), on a case small enough for full ncu captures."""
+    import torch
+    from paper_2112_13184_gb300 import ctm, inputs
+    d, D, chi = 3, 8, 64
+    c = ctm.CTMRG(d, D, chi, precision=ctm.CTM_OZAKI_BF16, ozaki_slices=5)
+    c.set_tensors(inputs.x_polarised_tensors(d, D, 0.05, seed=3))
+    c.set_envs(inputs.random_env(chi, [D] * 4, seed=4))
+    c.sweep(1)
+    torch.cuda.synchronize()
+    print("sweep_mixed_chi64 done", c.measure1(0, inputs.spin_ops(d)["Sx"]))
+    c.close()
+
+
+CASES = {"split_e": split_e, "sweep_mixed_chi64": sweep_mixed_chi64, "apply_fp64": apply_fp64, "apply_oz": apply_oz, "x2_oz": x2_oz, "x3_oz": x3_oz, "x4t_oz": x4t_oz}
 
 if __name__ == "__main__":
     if len(sys.argv) != 2 or sys.argv[1] not in CASES:
