@@ -83,8 +83,6 @@ struct ctm_ctx {
     double *Rb = nullptr, *G = nullptr, *Us = nullptr, *Ws = nullptr, *Sv = nullptr, *inv = nullptr;
     double *Uc = nullptr, *Vc = nullptr, *t1 = nullptr, *t2 = nullptr;
     // Cholesky-QR scratch (k x k) and the first-pass basis (N x k)
-    double *cq_G = nullptr, *cq_R1 = nullptr, *cq_R1i = nullptr, *cq_R2 = nullptr, *cq_R2i = nullptr,
-           *cq_d = nullptr, *cq_Q1 = nullptr;
     double *newC1 = nullptr, *newC4 = nullptr, *newT4 = nullptr, *tmpT = nullptr;
     double *Lh = nullptr, *Rh = nullptr, *rho = nullptr, *spec = nullptr, *corners = nullptr;
     double* splitk = nullptr;  // split-K partial sums
@@ -200,7 +198,6 @@ size_t footprint(int d, int D, const ctm_options& o) {
     dbl += 6 * z.Nk;                 // Om, Y, Z, Qm, Qm2, Qb
     dbl += 4 * z.kk + 2 * (size_t)k; // Rb, G, Us, Ws, Sv, inv
     dbl += z.Nchi + 3 * std::max(z.Nk, z.Nchi);  // Uc; Vc, t1, t2
-    dbl += 5 * z.kk + k + z.Nk;      // Cholesky-QR scratch
     dbl += 2 * z.C + 2 * z.T;        // newC1, newC4, newT4, tmpT
     dbl += 2 * z.Nchi * d * d;       // Lh, Rh
     dbl += std::max<size_t>(64 * 64, (size_t)d * d * d * d) + 2 * 16 * z.C;  // rho, spectra, corners
@@ -393,59 +390,6 @@ ctm_status qr_(ctm_ctx* h, const double* Y, double* Q, double* R) {
     prof_end(h, ev, P_QR, 4.0 * h->N * (double)h->k * h->k, 0.0);
     return CTM_OK;
 }
-// G = Y^T Y (k x k) of an N x k basis, always in FP64
-ctm_status gram(ctm_ctx* h, const double* Y, double* G) {
-    const int N = h->N, k = h->k;
-    const size_t ev = prof_begin(h);
-    CK(ctm::dgemm(true, false, k, k, N, 1.0, Y, k, Y, k, 0.0, G, k, h->stream, h->splitk, h->splitk_n));
-    prof_end(h, ev, P_GEMM, 2.0 * k * (double)k * N, 8.0 * ((double)N * k + (double)k * k));
-    return CTM_OK;
-}
-
-// Column-equilibrated Cholesky QR, two passes (CholQR2): for the bases of a
-// warm-started range finder, whose columns are close to orthogonal with
-// graded norms, it is as accurate as Householder and is GEMM work.
-//   G = Y^T Y, D ~ diag(G)^1/2 (powers of two), D^-1 G D^-1 = R1'^T R1',
-//   Q1 = Y D^-1 R1'^-1, Q1^T Q1 + s2 I = R2^T R2, Q = Q1 R2^-1, R = R2 R1' D.
-// Both passes shift the diagonal by 1e-14 of its mean: a warm basis of a
-// low-rank M has columns that M maps to rounding noise, Q1 then has a
-// condition number near 1/sqrt(shift), and an unshifted second pass meets
-// negative pivots.  The shift leaves Q orthonormal to ~1e-14 on every
-// direction M resolves and shortens only the noise columns, which the
-// singular-value cutoff removes.  Both Gram matrices are formed in FP64
-// whatever the precision: the shift keeps the factorisation positive only
-// while G is accurate to about that level, and an emulated Gram (error
-// ~2^-27 |y_i||y_j|) is not.
-ctm_status qr_chol(ctm_ctx* h, const double* Y, double* Q, double* R) {
-    ProfTag tg(h, "qr");
-    const int N = h->N, k = h->k;
-    const double kk = (double)k * k * k;
-    CKS(gram(h, Y, h->cq_G));
-    {
-        ProfTag t1(h, "qr.chol1");
-        const size_t ev = prof_begin(h);
-        CK(ctm::equilibrate(h->cq_G, k, h->cq_d, h->stream));
-        CK(ctm::chol_inv(h->cq_G, k, 1e-14, h->cq_R1, h->cq_R1i, h->stream));
-        CK(ctm::scale_rc(h->cq_R1i, k, h->cq_d, true, true, h->stream));  // D^-1 R1'^-1
-        prof_end(h, ev, P_QR, 2.0 * kk / 3.0, 0.0);
-    }
-    CKS(gemm(h, false, false, N, k, k, Y, k, h->cq_R1i, k, h->cq_Q1, k));
-    CKS(gram(h, h->cq_Q1, h->cq_G));
-    {
-        ProfTag t2(h, "qr.chol2");
-        const size_t ev = prof_begin(h);
-        CK(ctm::chol_inv(h->cq_G, k, 1e-14, h->cq_R2, h->cq_R2i, h->stream));
-        prof_end(h, ev, P_QR, 2.0 * kk / 3.0, 0.0);
-    }
-    CKS(gemm(h, false, false, N, k, k, h->cq_Q1, k, h->cq_R2i, k, Q, k));
-    ProfTag t3(h, "qr.r");
-    const size_t ev = prof_begin(h);
-    CK(ctm::scale_rc(h->cq_R1, k, h->cq_d, false, false, h->stream));  // R1' D
-    CK(ctm::dgemm(false, false, k, k, k, 1.0, h->cq_R2, k, h->cq_R1, k, 0.0, R, k, h->stream));
-    prof_end(h, ev, P_QR, 2.0 * kk, 0.0);
-    return CTM_OK;
-}
-
 ctm_status svd_(ctm_ctx* h) {
     ProfTag tg(h, "svd");
     const size_t ev = prof_begin(h);
@@ -561,9 +505,11 @@ ctm_status projectors(ctm_ctx* h, int slot, int cut) {
     if (warm) Om = h->warmV[cut];  // one more subspace iteration from last sweep's basis
     else CK(ctm::rng_normal(h->Om, (size_t)N * k, h->opt.seed, h->rng_counter++, h->stream));
     CKS(applyM(h, Om, h->Yb, k));
-    const bool chol = warm && k <= 160;  // warm bases: Cholesky QR; cold: Householder
-    if (chol) CKS(qr_chol(h, h->Yb, h->Qm, h->Rb));
-    else CKS(qr_(h, h->Yb, h->Qm, h->Rb));
+    // Householder QR for every basis: a Gram-based (Cholesky) QR resolves
+    // only directions above ~1e-8 of the largest, while the 1e-12 cutoff keeps
+    // directions down to 1e-12; with a warm basis that lags a still-changing
+    // environment that loss stopped the D=8, chi=128 iteration converging.
+    CKS(qr_(h, h->Yb, h->Qm, h->Rb));
     for (int it = 0; it < q; ++it) {
         CKS(applyMT(h, h->Qm, h->Zb, k));
         CKS(qr_(h, h->Zb, h->Qm2, h->Rb));
@@ -572,8 +518,7 @@ ctm_status projectors(ctm_ctx* h, int slot, int cut) {
     }
     // B^T = M^T Q = Q_b R_b  ->  B = R_b^T Q_b^T ; SVD(R_b^T) = U' S W^T
     CKS(applyMT(h, h->Qm, h->Zb, k));
-    if (chol) CKS(qr_chol(h, h->Zb, h->Qb, h->Rb));
-    else CKS(qr_(h, h->Zb, h->Qb, h->Rb));
+    CKS(qr_(h, h->Zb, h->Qb, h->Rb));
     CKS(perm(h, h->Rb, h->G, {k, k}, {1, 0}));
     CKS(svd_(h));
     // U = Q U'[:, :chi].  V = Q_b W over all k columns, sorted by singular
@@ -907,8 +852,6 @@ ctm_status ctm_create(int d, int D, const ctm_options* o, void* stream, ctm_hand
     A_(&h->Sv, h->k); A_(&h->inv, h->k);
     const size_t tk = std::max(z.Nk, z.Nchi);
     A_(&h->Uc, z.Nchi); A_(&h->Vc, z.Nk); A_(&h->t1, tk); A_(&h->t2, tk);
-    A_(&h->cq_G, z.kk); A_(&h->cq_R1, z.kk); A_(&h->cq_R1i, z.kk); A_(&h->cq_R2, z.kk); A_(&h->cq_R2i, z.kk);
-    A_(&h->cq_d, h->k); A_(&h->cq_Q1, z.Nk);
     A_(&h->newC1, z.C); A_(&h->newC4, z.C); A_(&h->newT4, z.T); A_(&h->tmpT, z.T);
     A_(&h->Lh, z.Nchi * d * d); A_(&h->Rh, z.Nchi * d * d);
     A_(&h->rho, std::max<size_t>(64 * 64, (size_t)d * d * d * d));

@@ -41,12 +41,6 @@ cudaError_t dot(const double* x, const double* y, size_t n, double* result, cuda
 // ---- dense linear algebra (linalg.cu) ---------------------------------------
 size_t qr_ws_bytes(int N, int k);
 cudaError_t qr(const double* Y, int N, int k, double* Q, double* R, void* ws, cudaStream_t s);
-// G + shift_rel*mean(diag) I = R^T R; R upper, Rinv = R^{-1} (k <= 160, k x k row-major)
-cudaError_t chol_inv(const double* G, int k, double shift_rel, double* R, double* Rinv, cudaStream_t s);
-// d_i = sqrt(G_ii); G <- D^-1 G D^-1 (k <= 1024)
-cudaError_t equilibrate(double* G, int k, double* d, cudaStream_t s);
-// scale rows (or columns) of a k x k matrix by w (or divide by it)
-cudaError_t scale_rc(double* X, int k, const double* w, bool rows, bool inv, cudaStream_t s);
 size_t svd_ws_bytes(int k);
 cudaError_t svd(const double* G, int k, double* U, double* S, double* V, void* ws, cudaStream_t s);
 // svd() with its workspace in a static device array (k <= svd_noalloc_max_k())

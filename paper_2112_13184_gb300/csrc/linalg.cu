@@ -271,127 +271,6 @@ __global__ void __launch_bounds__(256) k_jacobi_cluster(double* __restrict__ Gt,
     }
 }
 
-// ---------------------------------------------------------------------------
-// Cholesky factor and its inverse of a small SPD matrix (one CTA, k <= 160,
-// the matrix in shared memory).  G + shift I = R^T R with R upper triangular
-// and positive diagonal; pivots below 1e-30 of the mean diagonal are clamped.
-//
-// GB300 issues FP64 at a small fraction of its FP32 rate, so the kernel is
-// organised around few FP64 instructions and one barrier per step:
-//  - right-looking upper Cholesky on the unscaled rows: step j subtracts
-//    S[j][a] S[j][b] / piv_j from the trailing upper triangle, one warp per
-//    row a, lanes along b (contiguous, conflict-free); rows are scaled by
-//    1/sqrt(piv) once at the end;
-//  - the next pivot's 1/sqrt is taken by the lane that has just updated it:
-//    a single-precision estimate refined by two Newton steps for 1/sqrt(p),
-//    r <- r (3 - p r^2) / 2;
-//  - L^-1 (L = R^T) by right-looking substitution B_m -= (R_im / R_ii) B_i
-//    in the lower triangle (B = I initially, X_i = B_i / R_ii), again one
-//    warp per row; R^-1 = (L^-1)^T.
-// ---------------------------------------------------------------------------
-// 1/sqrt(p) for a normal p > 0: p = m 4^h with m in [1, 4) taken from the
-// exponent field, seed rsqrtf(m) 2^-h, then two Newton steps
-__device__ __forceinline__ double rsqrt_newton(double p) {
-    const long long bits = __double_as_longlong(p);
-    const int h = ((int)((bits >> 52) & 0x7ff) - 1023) >> 1;
-    const double m = __longlong_as_double(bits - ((long long)(2 * h) << 52));
-    double r = __longlong_as_double(__double_as_longlong((double)rsqrtf((float)m)) - ((long long)h << 52));
-#pragma unroll
-    for (int it = 0; it < 2; ++it) r = r * fma(-0.5 * p, r * r, 1.5);
-    return r;
-}
-
-__global__ void __launch_bounds__(1024) k_chol_inv(const double* __restrict__ G, int k, double shift_rel,
-                                                  double* __restrict__ R, double* __restrict__ Rinv) {
-    extern __shared__ double S[];   // k*k, then ri[k] = 1/R_jj, dg[k] = R_jj, rp[k] = 1/piv_j
-    double* ri = S + (size_t)k * k;
-    double* dg = ri + k;
-    double* rp = dg + k;
-    __shared__ double sm[32];
-    __shared__ double clamp;
-    const int tid = threadIdx.x, nt = blockDim.x, warp = tid >> 5, lane = tid & 31, nw = nt >> 5;
-    double tr = 0.0;
-    for (int t = tid; t < k * k; t += nt) {
-        const int i = t / k, j = t - i * k;
-        const double v = j >= i ? G[t] : 0.0;  // upper triangle of the symmetric G, lower zeroed
-        S[t] = v;
-        if (i == j) tr += v;
-    }
-    tr = block_sum(tr, sm);
-    const double mean = tr > 0.0 ? tr / k : 1.0;
-    for (int i = tid; i < k; i += nt) S[(size_t)i * k + i] += shift_rel * mean;
-    if (tid == 0) clamp = 1e-30 * mean;
-    __syncthreads();
-    auto pivot = [&](int j) {
-        double p = S[(size_t)j * k + j];
-        if (!(p > clamp)) p = clamp;
-        const double r = rsqrt_newton(p);
-        ri[j] = r;
-        dg[j] = p * r;
-        rp[j] = r * r;
-    };
-    if (tid == 0) pivot(0);
-    __syncthreads();
-    for (int j = 0; j < k; ++j) {
-        const double* Sj = S + (size_t)j * k;
-        const double q = rp[j];
-        for (int a = j + 1 + warp; a < k; a += nw) {
-            const double f = Sj[a] * q;
-            double* Sa = S + (size_t)a * k;
-            for (int b = a + lane; b < k; b += 32) Sa[b] = fma(-f, Sj[b], Sa[b]);
-            if (a == j + 1 && lane == 0) pivot(a);  // this lane has just finished S[a][a]
-        }
-        __syncthreads();
-    }
-    // R: upper rows scaled by 1/sqrt(piv), diagonal sqrt(piv)
-    for (int t = tid; t < k * k; t += nt) {
-        const int i = t / k, j = t - i * k;
-        if (j > i) S[t] *= ri[i];
-        else if (j == i) S[t] = dg[i];
-    }
-    __syncthreads();
-    // B (rows of L^-1 before their 1/R_ii scaling) in the zeroed strict lower triangle
-    for (int i = 0; i < k; ++i) {
-        const double* Si = S + (size_t)i * k;
-        const double rii = ri[i];
-        for (int m = i + 1 + warp; m < k; m += nw) {
-            const double g = Si[m] * rii;  // L[m][i] / L[i][i]
-            double* Sm = S + (size_t)m * k;
-            for (int c = lane; c <= i; c += 32) Sm[c] = fma(-g, c == i ? 1.0 : Si[c], Sm[c]);
-        }
-        __syncthreads();
-    }
-    for (int t = tid; t < k * k; t += nt) {
-        const int i = t / k, j = t - i * k;
-        R[t] = j >= i ? S[t] : 0.0;
-        // R^-1[i][j] = (L^-1)[j][i] = B[j][i] / R_jj
-        Rinv[t] = j > i ? S[(size_t)j * k + i] * ri[j] : (j == i ? ri[i] : 0.0);
-    }
-}
-
-// d_i = 2^floor(log2(G_ii) / 2) (1 for a zero or non-normal diagonal);
-// G <- D^-1 G D^-1, exact since D holds powers of two
-__global__ void k_equilibrate(double* __restrict__ G, int k, double* __restrict__ d) {
-    __shared__ double rd[1024];
-    for (int i = threadIdx.x; i < k; i += blockDim.x) {
-        const double v = G[(size_t)i * k + i];
-        const int be = (int)((__double_as_longlong(v) >> 52) & 0x7ff);
-        const int e = (v > 0.0 && be > 0 && be < 2047) ? (be - 1023) >> 1 : 0;
-        d[i] = __longlong_as_double((long long)(1023 + e) << 52);
-        rd[i] = __longlong_as_double((long long)(1023 - e) << 52);
-    }
-    __syncthreads();
-    for (int t = threadIdx.x; t < k * k; t += blockDim.x) G[t] *= rd[t / k] * rd[t % k];
-}
-
-// X[i][j] *= (rows ? w[i] : w[j]) ; with inv, divide instead
-__global__ void k_scale_rc(double* __restrict__ X, int k, const double* __restrict__ w, int rows, int inv) {
-    for (int t = blockIdx.x * blockDim.x + threadIdx.x; t < k * k; t += gridDim.x * blockDim.x) {
-        const double f = w[rows ? t / k : t % k];
-        X[t] = inv ? X[t] / f : X[t] * f;
-    }
-}
-
 inline unsigned grid_for(size_t n, unsigned threads = 256) {
     size_t b = (n + threads - 1) / threads;
     if (b > 152 * 32) b = 152 * 32;
@@ -701,34 +580,6 @@ cudaError_t svd_noalloc(const double* G, int k, double* U, double* S, double* V,
         ws = g_scratch_ptr[dev];
     }
     return svd(G, k, U, S, V, ws, s);
-}
-
-cudaError_t chol_inv(const double* G, int k, double shift_rel, double* R, double* Rinv, cudaStream_t s) {
-    if (k <= 0 || k > 160) return cudaErrorInvalidValue;
-    const size_t smem = sizeof(double) * ((size_t)k * k + 3 * k);
-    static bool attr = false;
-    if (!attr) {
-        cudaError_t e = cudaFuncSetAttribute(k_chol_inv, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                             (int)(sizeof(double) * (160 * 160 + 3 * 160)));
-        if (e) return e;
-        attr = true;
-    }
-    ++g_launches;
-    k_chol_inv<<<1, 1024, smem, s>>>(G, k, shift_rel, R, Rinv);
-    return cudaGetLastError();
-}
-
-cudaError_t equilibrate(double* G, int k, double* d, cudaStream_t s) {
-    if (k <= 0 || k > 1024) return cudaErrorInvalidValue;
-    ++g_launches;
-    k_equilibrate<<<1, 1024, 0, s>>>(G, k, d);
-    return cudaGetLastError();
-}
-
-cudaError_t scale_rc(double* X, int k, const double* w, bool rows, bool inv, cudaStream_t s) {
-    ++g_launches;
-    k_scale_rc<<<grid_for((size_t)k * k), 256, 0, s>>>(X, k, w, rows ? 1 : 0, inv ? 1 : 0);
-    return cudaGetLastError();
 }
 
 }  // namespace ctm
