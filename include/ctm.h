@@ -120,6 +120,28 @@ ctm_status ctm_sweep(ctm_handle h, int n);
  * output pointer may be NULL.  Returns CTM_NOT_CONVERGED at the cap. */
 ctm_status ctm_run(ctm_handle h, int* sweeps_done, double* last_delta);
 
+/* Asynchronous form of ctm_sweep: enqueues n sweeps on the handle's stream
+ * and returns without waiting.  Non-finite values or a timed-out device
+ * wait are reported by the next synchronising call on the handle
+ * (ctm_sync, ctm_spectrum_delta, ctm_sweep, ...).  Lets several handles,
+ * each on its own stream, run at the same time on one GPU. */
+ctm_status ctm_sweep_async(ctm_handle h, int n);
+
+/* Waits for the handle's stream and reports any error its sweeps raised. */
+ctm_status ctm_sync(ctm_handle h);
+
+/* Batched sweeps: advances n independent instances by `sweeps` sweeps each.
+ * Sweeps are issued round-robin over the handles (each on its own stream,
+ * each steady sweep one CUDA-graph launch), so small instances overlap on
+ * the GPU; then every handle is synchronised.  Returns the first error met
+ * (all handles are still synchronised).  Handles must be distinct. */
+ctm_status ctm_batch_sweep(const ctm_handle* hs, int n, int sweeps);
+
+/* Convergence measure of Sec. 2.2 as ctm_run applies it: the max-abs change
+ * of the normalised corner spectra since this handle's previous call
+ * (+infinity on the first call).  Synchronises the handle. */
+ctm_status ctm_spectrum_delta(ctm_handle h, double* delta);
+
 /* Normalised singular values (sum 1) of every corner: out[site][corner][chi]. */
 ctm_status ctm_corner_spectra(ctm_handle h, double* out_host);
 

@@ -62,6 +62,7 @@ const FrameMaps FM;
 }  // namespace
 
 struct ctm_ctx {
+    std::vector<double> last_spec;  // corner spectra at the previous ctm_spectrum_delta
     int d = 0, D = 0, chi = 0, N = 0, k = 0, q = 0;
     ctm_options opt{};
     cudaStream_t stream = nullptr;
@@ -947,6 +948,58 @@ ctm_status ctm_sweep(ctm_handle h, int n) {
     const ctm_status st = read_flag(h);
     prof_collect(h);
     return st;
+}
+
+ctm_status ctm_sweep_async(ctm_handle h, int n) {
+    if (!h || n < 0) return CTM_ERR_ARG;
+    CKS(check_ready(h));
+    for (int s = 0; s < n; ++s) CKS(one_sweep(h));
+    return CTM_OK;
+}
+
+ctm_status ctm_sync(ctm_handle h) {
+    if (!h) return CTM_ERR_ARG;
+    const ctm_status st = read_flag(h);
+    prof_collect(h);
+    return st;
+}
+
+ctm_status ctm_batch_sweep(const ctm_handle* hs, int n, int sweeps) {
+    if (!hs || n < 0 || sweeps < 0) return CTM_ERR_ARG;
+    for (int i = 0; i < n; ++i) {
+        if (!hs[i]) return CTM_ERR_ARG;
+        for (int j = 0; j < i; ++j)
+            if (hs[j] == hs[i]) return CTM_ERR_ARG;
+        CKS(check_ready(hs[i]));
+    }
+    ctm_status first = CTM_OK;
+    for (int s = 0; s < sweeps && first == CTM_OK; ++s)
+        for (int i = 0; i < n; ++i) {
+            const ctm_status st = one_sweep(hs[i]);
+            if (st != CTM_OK && first == CTM_OK) first = st;
+        }
+    for (int i = 0; i < n; ++i) {
+        const ctm_status st = read_flag(hs[i]);
+        prof_collect(hs[i]);
+        if (st != CTM_OK && first == CTM_OK) first = st;
+    }
+    return first;
+}
+
+ctm_status ctm_spectrum_delta(ctm_handle h, double* delta) {
+    if (!h || !delta) return CTM_ERR_ARG;
+    CKS(check_ready(h));
+    CKS(read_flag(h));
+    std::vector<double> cur;
+    CKS(spectra(h, cur));
+    double d = INFINITY;
+    if (h->last_spec.size() == cur.size()) {
+        d = 0.0;
+        for (size_t i = 0; i < cur.size(); ++i) d = std::max(d, std::fabs(cur[i] - h->last_spec[i]));
+    }
+    h->last_spec.swap(cur);
+    *delta = d;
+    return CTM_OK;
 }
 
 ctm_status ctm_run(ctm_handle h, int* sweeps_done, double* last_delta) {

@@ -205,7 +205,7 @@ __device__ __forceinline__ void digits(double x, int e, int s, int* d) {
     for (int t = MAX_S - 1; t >= 1; --t) {
         if (t < s) {
             const long long Yn = (Y + 128) >> 8;
-            d[t] = (int)Y - ((int)Yn << 8);
+            d[t] = (int)((uint32_t)Y - ((uint32_t)Yn << 8));  // Y - 256 Y', in [-128, 127]
             Y = Yn;
         } else {
             d[t] = 0;

@@ -62,6 +62,10 @@ _sig("ctm_set_tensor", c_int, c_void_p, c_int, c_void_p, c_int)
 _sig("ctm_set_env", c_int, c_void_p, c_int, c_int, c_void_p, c_int)
 _sig("ctm_get_env", c_int, c_void_p, c_int, c_int, c_void_p, c_int)
 _sig("ctm_sweep", c_int, c_void_p, c_int)
+_sig("ctm_sweep_async", c_int, c_void_p, c_int)
+_sig("ctm_sync", c_int, c_void_p)
+_sig("ctm_batch_sweep", c_int, ctypes.POINTER(c_void_p), c_int, c_int)
+_sig("ctm_spectrum_delta", c_int, c_void_p, c_dp)
 _sig("ctm_run", c_int, c_void_p, c_ip, c_dp)
 _sig("ctm_corner_spectra", c_int, c_void_p, c_dp)
 _sig("ctm_rdm1", c_int, c_void_p, c_int, c_dp)
@@ -179,6 +183,28 @@ def ctm_get_env(h, site, which, shape):
 
 def ctm_sweep(h, n):
     _check(_lib.ctm_sweep(h, n), h)
+
+
+def ctm_sweep_async(h, n):
+    _check(_lib.ctm_sweep_async(h, n), h)
+
+
+def ctm_sync(h):
+    _check(_lib.ctm_sync(h), h)
+
+
+def ctm_batch_sweep(hs, sweeps):
+    arr = (c_void_p * len(hs))(*hs)
+    st = _lib.ctm_batch_sweep(arr, len(hs), sweeps)
+    if st < 0:
+        raise CtmError(st, "batched sweep failed: " + "; ".join(
+            _lib.ctm_last_error(h).decode(errors="replace") for h in hs))
+
+
+def ctm_spectrum_delta(h):
+    d = c_double()
+    _check(_lib.ctm_spectrum_delta(h, ctypes.byref(d)), h)
+    return d.value
 
 
 def ctm_run(h):
@@ -344,6 +370,15 @@ class CTMRG:
 
     def sweep(self, n):
         ctm_sweep(self.h, n)
+
+    def sweep_async(self, n):
+        ctm_sweep_async(self.h, n)
+
+    def sync(self):
+        ctm_sync(self.h)
+
+    def spectrum_delta(self):
+        return ctm_spectrum_delta(self.h)
 
     def run(self):
         return ctm_run(self.h)

@@ -230,3 +230,36 @@ def workload(name: str):
         return dict(As=As, envs=envs, chi=chi, d=d, D=D, sweeps=20,
                     op1=spin_ops(3)["Sx"], op2=blbq_bond(3, 1.0, 0.1))
     raise KeyError(name)
+
+
+def serving_request(j: int, ds=(2, 3), Ds=(4, 6, 8), chis=(32, 64, 128)):
+    """Request j of the serving workload (a field / coupling scan family):
+    d, D, chi drawn from seed 10000 + j; d = 2: spin-1/2 polarised along +x
+    with the transverse-field Ising bond; d = 3: soft-core bosons (n_max = 2)
+    in the uniform state with the boson bond; product state + 0.05 N(0, 1)
+    noise; random environment from the same seed."""
+    rng = np.random.default_rng(10000 + j)
+    d = int(rng.choice(ds))
+    D = int(rng.choice(Ds))
+    chi = int(rng.choice(chis))
+    if d == 2:
+        As = x_polarised_tensors(2, D, 0.05, seed=10000 + j)
+        op1, op2 = spin_ops(2)["Sx"], tfim_bond(2)
+    else:
+        As = uniform_boson_tensors(2, D, 0.05, seed=10000 + j)
+        op1, op2 = boson_ops(2)["n"], boson_bond(2)
+    envs = random_env(chi, [D] * 4, seed=20000 + j)
+    return dict(d=d, D=D, chi=chi, As=As, envs=envs, op1=op1, op2=op2)
+
+
+def batch_instance(i: int):
+    """Instance i of the batched workload (64 uneven instances): seed 100 + i
+    draws D in {3, 4, 5, 6}, then chi in {24, 32, 48, 64}; d = 2 Neel + 0.1
+    N(0, 1) noise; environment from seed 200 + i."""
+    rng = np.random.default_rng(100 + i)
+    D = int(rng.choice((3, 4, 5, 6)))
+    chi = int(rng.choice((24, 32, 48, 64)))
+    As = neel_tensors(2, D, 0.1, seed=100 + i)
+    envs = random_env(chi, [D] * 4, seed=200 + i)
+    return dict(d=2, D=D, chi=chi, As=As, envs=envs, op1=spin_ops(2)["Sz"], op2=heisenberg_bond(2))
+
