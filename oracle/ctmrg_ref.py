@@ -20,7 +20,7 @@ so that P_dn P_up = 1 (kept part) and H_u^T P_up P_dn H_d = U_chi S_chi V_chi^T.
 (The randomized / Arnoldi partial SVD the paper mentions is a faster way to
 reach the same truncated triplets and is not used here.)
 
-Readings where the paper is silent (all listed in the design doc):
+Readings where the paper is silent:
   * one sweep = left, top, right, bottom moves; each move visits the columns
     in order and, per column, computes the projectors of every row cut
     before updating any tensor (Corboz-style simultaneous row update);
