@@ -83,7 +83,6 @@ struct ctm_ctx {
     double *Om = nullptr, *Yb = nullptr, *Zb = nullptr, *Qm = nullptr, *Qm2 = nullptr, *Qb = nullptr;
     double *Rb = nullptr, *G = nullptr, *Us = nullptr, *Ws = nullptr, *Sv = nullptr, *inv = nullptr;
     double *Uc = nullptr, *Vc = nullptr, *t1 = nullptr, *t2 = nullptr;
-    // Cholesky-QR scratch (k x k) and the first-pass basis (N x k)
     double *newC1 = nullptr, *newC4 = nullptr, *newT4 = nullptr, *tmpT = nullptr;
     double *Lh = nullptr, *Rh = nullptr, *rho = nullptr, *spec = nullptr, *corners = nullptr;
     double* splitk = nullptr;  // split-K partial sums

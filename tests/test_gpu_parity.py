@@ -98,9 +98,9 @@ def test_neel_d2_D3_chi16_emulated_fp64(ctm, slices, tol):
 
 def test_neel_d2_D3_chi16_emulated_fp64_randomised(ctm):
     """Emulated FP64 through the warm-started randomised range finder (no
-    exact SVD): the warm sweeps orthonormalise their bases by Cholesky-QR2,
-    whose Gram matrices must stay accurate for the diagonal shift to keep
-    them positive.  Same |dE| <= 1e-8 bar as the exact-SVD path."""
+    exact SVD): every range-finder apply is an emulated product, every basis
+    is orthonormalised by Householder QR.  Same |dE| <= 1e-8 bar as the
+    exact-SVD path."""
     w = I.workload("neel_d2_D3_chi16")
     c, ref = run_both(ctm, w["As"], w["envs"], w["d"], w["D"], w["chi"], w["sweeps"],
                       precision=ctm.CTM_OZAKI_BF16, ozaki_slices=5, exact_svd_max_n=0)
@@ -115,9 +115,8 @@ def test_neel_d2_D3_chi16_emulated_fp64_randomised(ctm):
 @pytest.mark.parametrize("precision", ["fp64", "mixed"])
 def test_product_state_randomised_warm(ctm, precision):
     """A Neel product state has a rank-1 environment, so all but one column
-    of every warm range-finder basis lies in the null space of M: the
-    Cholesky-QR2 of the warm sweeps must stay finite and the observables
-    exact."""
+    of every warm range-finder basis lies in the null space of M: the warm
+    sweeps' orthonormalisation must stay finite and the observables exact."""
     As = I.neel_tensors(2, 3, 0.0, seed=0)
     envs = I.random_env(16, [3] * 4, seed=1)
     prec = ctm.CTM_OZAKI_BF16 if precision == "mixed" else ctm.CTM_FP64
