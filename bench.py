@@ -48,6 +48,21 @@ def parse():
     return ap.parse_args()
 
 
+def max_over_ranks(x, world, device):
+    """Largest x over all ranks: a replicated job takes as long as its
+    slowest rank."""
+    import torch
+    t = torch.tensor([float(x)], dtype=torch.float64, device=device)
+    if world > 1:
+        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+    return float(t.item())
+
+
+def replica_throughput(units_per_rank, world, seconds_max):
+    """Whole-job throughput of `world` independent replicas, timed by the slowest."""
+    return world * units_per_rank / seconds_max
+
+
 def dist_env():
     rank = int(os.environ.get("RANK", "0"))
     world = int(os.environ.get("WORLD_SIZE", "1"))
@@ -256,11 +271,8 @@ def run_ours(args):
     by_op = C.ctm_profile_report(solver.h)
     prof = C.ctm_profile_read(solver.h, reset=True)
     C.ctm_profile_enable(solver.h, False)
-    t = torch.tensor([ms], device="cuda")
-    if world > 1:
-        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-    ms_max = float(t.item())
-    value = world * args.steps / (ms_max / 1e3)
+    ms_max = max_over_ranks(ms, world, "cuda")
+    value = replica_throughput(args.steps, world, ms_max / 1e3)
 
     # end to end through the C ABI with host buffers: per step copy A and the
     # environment in from pinned host memory, one sweep, environment out
@@ -283,10 +295,8 @@ def run_ours(args):
                 v.copy_(torch.from_numpy(C.ctm_get_env(solver.h, i, k, tuple(v.shape))))
     barrier()
     e2e_s = time.perf_counter() - t0
-    te = torch.tensor([e2e_s], device="cuda")
-    if world > 1:
-        torch.distributed.all_reduce(te, op=torch.distributed.ReduceOp.MAX)
-    e2e_value = world * args.e2e_steps / float(te.item()) if args.e2e_steps > 0 else None
+    e2e_max = max_over_ranks(e2e_s, world, "cuda")
+    e2e_value = replica_throughput(args.e2e_steps, world, e2e_max) if args.e2e_steps > 0 else None
 
     if rank == 0:
         g = prof["gemm"]
