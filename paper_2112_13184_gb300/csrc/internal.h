@@ -22,21 +22,17 @@ cudaError_t dgemm(bool tA, bool tB, int M, int N, int K, double alpha, const dou
                   double* ws = nullptr, size_t ws_doubles = 0);
 cudaError_t permute(const double* src, double* dst, int ndim, const int* dims, const int* perm,
                     cudaStream_t s);
-cudaError_t copy(double* dst, const double* src, size_t n, cudaStream_t s);
-cudaError_t fill(double* dst, double v, size_t n, cudaStream_t s);
 // X[r*ld + c] *= w[c], r < rows, c < cols
 cudaError_t scale_cols(double* X, int rows, int cols, int ld, const double* w, cudaStream_t s);
 // w[j] = s[j] > cut*s[0] ? 1/sqrt(s[j]) : 0
 cudaError_t inv_sqrt_cut(const double* sv, double* w, int n, double cut, cudaStream_t s);
 // bits of max|x| into *maxbits (must be zeroed first); sticky
 cudaError_t maxabs(const double* x, size_t n, unsigned long long* maxbits, cudaStream_t s);
-// x /= max (skips when max is 0); sets *flag = 1 if max is not finite
+// x /= max; sets *flag = 1 if max is not finite, 2 (when still 0) if max is 0
 cudaError_t scale_by_max(double* x, size_t n, const unsigned long long* maxbits, int* flag,
                          cudaStream_t s);
 // out[i] = standard normal, Philox4x32-10 counter (seed, stream_id, i)
 cudaError_t rng_normal(double* out, size_t n, uint64_t seed, uint64_t stream_id, cudaStream_t s);
-// result[0] = sum_i x[i] * y[i] (single CTA reduction, n small-ish)
-cudaError_t dot(const double* x, const double* y, size_t n, double* result, cudaStream_t s);
 
 // ---- dense linear algebra (linalg.cu) ---------------------------------------
 size_t qr_ws_bytes(int N, int k);

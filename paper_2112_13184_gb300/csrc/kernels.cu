@@ -209,14 +209,6 @@ cudaError_t permute(const double* src, double* dst, int ndim, const int* dims, c
 // elementwise helpers
 // ---------------------------------------------------------------------------
 namespace {
-__global__ void k_copy(double* __restrict__ d, const double* __restrict__ s, size_t n) {
-    for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x)
-        d[i] = s[i];
-}
-__global__ void k_fill(double* __restrict__ d, double v, size_t n) {
-    for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x)
-        d[i] = v;
-}
 __global__ void k_scale_cols(double* X, int rows, int cols, int ld, const double* __restrict__ w) {
     const size_t total = (size_t)rows * cols;
     for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < total; i += (size_t)gridDim.x * blockDim.x) {
@@ -301,21 +293,6 @@ __global__ void k_rng_normal(double* __restrict__ out, size_t n, uint64_t seed, 
         if (2 * p + 1 < n) out[2 * p + 1] = rad * sn;
     }
 }
-__global__ void k_dot(const double* __restrict__ x, const double* __restrict__ y, size_t n, double* res) {
-    double acc = 0.0;
-    for (size_t i = threadIdx.x; i < n; i += blockDim.x) acc = fma(x[i], y[i], acc);
-    for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
-    __shared__ double sm[32];
-    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
-    if (lane == 0) sm[w] = acc;
-    __syncthreads();
-    if (w == 0) {
-        acc = (lane < (int)(blockDim.x >> 5)) ? sm[lane] : 0.0;
-        for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
-        if (lane == 0) *res = acc;
-    }
-}
-
 inline unsigned grid_for(size_t n, unsigned threads = 256) {
     size_t b = (n + threads - 1) / threads;
     if (b > 152 * 32) b = 152 * 32;
@@ -324,18 +301,6 @@ inline unsigned grid_for(size_t n, unsigned threads = 256) {
 }
 }  // namespace
 
-cudaError_t copy(double* dst, const double* src, size_t n, cudaStream_t s) {
-    if (!n) return cudaSuccess;
-    ++g_launches;
-    k_copy<<<grid_for(n), 256, 0, s>>>(dst, src, n);
-    return cudaGetLastError();
-}
-cudaError_t fill(double* dst, double v, size_t n, cudaStream_t s) {
-    if (!n) return cudaSuccess;
-    ++g_launches;
-    k_fill<<<grid_for(n), 256, 0, s>>>(dst, v, n);
-    return cudaGetLastError();
-}
 cudaError_t scale_cols(double* X, int rows, int cols, int ld, const double* w, cudaStream_t s) {
     if (rows <= 0 || cols <= 0) return cudaSuccess;
     ++g_launches;
@@ -363,11 +328,6 @@ cudaError_t rng_normal(double* out, size_t n, uint64_t seed, uint64_t sid, cudaS
     if (!n) return cudaSuccess;
     ++g_launches;
     k_rng_normal<<<grid_for((n + 1) / 2), 256, 0, s>>>(out, n, seed, sid);
-    return cudaGetLastError();
-}
-cudaError_t dot(const double* x, const double* y, size_t n, double* result, cudaStream_t s) {
-    ++g_launches;
-    k_dot<<<1, 1024, 0, s>>>(x, y, n, result);
     return cudaGetLastError();
 }
 
