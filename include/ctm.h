@@ -124,7 +124,9 @@ ctm_status ctm_sweep(ctm_handle h, int n);
  * agree with the FP64 path to ~1e-8. */
 ctm_status ctm_run(ctm_handle h, int* sweeps_done, double* last_delta);
 
-/* Asynchronous form of ctm_sweep: enqueues n sweeps on the handle's stream
+/* Asynchronous form of ctm_sweep (sweep of Sec. 2.2; the asynchronous and
+ * batched forms below serve many instances at once and have no counterpart
+ * in the paper): enqueues n sweeps on the handle's stream
  * and returns without waiting.  Non-finite values or a timed-out device
  * wait are reported by the next synchronising call on the handle
  * (ctm_sync, ctm_spectrum_delta, ctm_sweep, ...).  Lets several handles,
