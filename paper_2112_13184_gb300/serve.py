@@ -31,8 +31,8 @@ import argparse
 import json
 import time
 from collections import deque
-from dataclasses import dataclass, field
-from typing import Any, Callable, Deque, Dict, List, Optional
+from dataclasses import dataclass
+from typing import Any, Callable, Deque, Dict, List
 
 import numpy as np
 
@@ -166,6 +166,23 @@ class Server:
         self.done.extend(finished)
         self._admit()
         return finished
+
+    def cancel(self, rid: int) -> bool:
+        """Withdraws a request: a waiting one is dropped, an active one has
+        its handle freed between steps (none of its work is in flight then).
+        Returns False when the request is unknown or already finished."""
+        for r in list(self.waiting):
+            if r.rid == rid:
+                self.waiting.remove(r)
+                return True
+        for a in self.active:
+            if a.req.rid == rid:
+                self.backend.close(a.handle)
+                self.in_use -= a.bytes
+                self.active.remove(a)
+                self._admit()
+                return True
+        return False
 
     def idle(self) -> bool:
         return not self.waiting and not self.active

@@ -78,6 +78,20 @@ def test_max_sweeps_and_stats():
     assert st["requests"] == 2 and st["converged"] == 1 and st["p99_s"] >= st["p50_s"]
 
 
+def test_cancel_waiting_and_active():
+    fb = FakeBackend({0: 60, 1: 60, 2: 30}, {0: 10 ** 9, 1: 1, 2: 1})
+    srv = Server(100, fb)
+    for i in range(3):
+        srv.submit(req(i))
+    srv.step()  # 0 active; 1 waits (no room), 2 waits behind it
+    assert srv.cancel(2) and [r.rid for r in srv.waiting] == [1]
+    assert srv.cancel(0)  # frees 60: 1 is admitted at once
+    assert fb.closed[:1] == [0] and [a.req.rid for a in srv.active] == [1]
+    res = srv.drain()
+    assert [r.rid for r in res] == [1] and srv.in_use == 0 and fb.live == 0
+    assert not srv.cancel(0) and not srv.cancel(7)
+
+
 def test_oversized_request_rejected():
     srv = Server(10, FakeBackend({0: 11}, {0: 1}))
     with pytest.raises(ValueError):
