@@ -42,6 +42,13 @@ import numpy as np
 
 ENV_NAMES = ("C1", "T1", "C2", "T2", "C3", "T3", "C4", "T4")
 
+# Multi-operand einsums are evaluated as a chain of pairwise contractions
+# with no cap on the size of the intermediates.  (numpy's default cap makes
+# it fold the last three operands of an enlarged corner into one unblocked
+# loop, which takes minutes at D = 8.)  This fixes only the order in which
+# the sum of each einsum is evaluated, not what it sums.
+PAIRWISE = ("greedy", 1 << 40)
+
 
 def _site(x, y, Lx, Ly):
     return (x % Lx) + Lx * (y % Ly)
@@ -64,28 +71,28 @@ def double_layer(A):
 # --------------------------------------------------------------------------
 def enlarged_ul(C1, T1, T4, A):
     """Upper-left: rows = down leg (T4.c_C4, A.d, A*.d), cols = right leg (T1.c_C2, A.r, A*.r)."""
-    Q = np.einsum("gh,huUb,alLg,slurd,sLURD->adDbrR", C1, T1, T4, A, A, optimize=True)
+    Q = np.einsum("gh,huUb,alLg,slurd,sLURD->adDbrR", C1, T1, T4, A, A, optimize=PAIRWISE)
     s = Q.shape
     return Q.reshape(s[0] * s[1] * s[2], s[3] * s[4] * s[5])
 
 
 def enlarged_ur(T1, C2, T2, A):
     """Upper-right: rows = left leg (T1.c_C1, A.l, A*.l), cols = down leg (T2.c_C3, A.d, A*.d)."""
-    Q = np.einsum("buUg,gh,hrRe,slurd,sLURD->blLedD", T1, C2, T2, A, A, optimize=True)
+    Q = np.einsum("buUg,gh,hrRe,slurd,sLURD->blLedD", T1, C2, T2, A, A, optimize=PAIRWISE)
     s = Q.shape
     return Q.reshape(s[0] * s[1] * s[2], s[3] * s[4] * s[5])
 
 
 def enlarged_br(T2, C3, T3, A):
     """Lower-right: rows = left leg (T3.c_C4, A.l, A*.l), cols = up leg (T2.c_C2, A.u, A*.u)."""
-    Q = np.einsum("erRg,gh,hdDz,slurd,sLURD->zlLeuU", T2, C3, T3, A, A, optimize=True)
+    Q = np.einsum("erRg,gh,hdDz,slurd,sLURD->zlLeuU", T2, C3, T3, A, A, optimize=PAIRWISE)
     s = Q.shape
     return Q.reshape(s[0] * s[1] * s[2], s[3] * s[4] * s[5])
 
 
 def enlarged_bl(T4, C4, T3, A):
     """Lower-left: rows = up leg (T4.c_C1, A.u, A*.u), cols = right leg (T3.c_C3, A.r, A*.r)."""
-    Q = np.einsum("glLa,hg,zdDh,slurd,sLURD->auUzrR", T4, C4, T3, A, A, optimize=True)
+    Q = np.einsum("glLa,hg,zdDh,slurd,sLURD->auUzrR", T4, C4, T3, A, A, optimize=PAIRWISE)
     s = Q.shape
     return Q.reshape(s[0] * s[1] * s[2], s[3] * s[4] * s[5])
 
@@ -160,10 +167,10 @@ def absorb_T4(T4, A, P_up_below, P_dn_above):
     """T4'[c1, r, r', c2] = P_up(cut below)[a_b, c1] (T4 A A*)[a_b, (r r'), a_t] P_dn(cut above)[c2, a_t].
 
     a_b = (T4.c_C4, A.d, A*.d), a_t = (T4.c_C1, A.u, A*.u)."""
-    X = np.einsum("alLg,slurd,sLURD->adDrRguU", T4, A, A, optimize=True)
+    X = np.einsum("alLg,slurd,sLURD->adDrRguU", T4, A, A, optimize=PAIRWISE)
     s = X.shape
     X = X.reshape(s[0] * s[1] * s[2], s[3], s[4], s[5] * s[6] * s[7])
-    return np.einsum("ac,arRb,eb->crRe", P_up_below, X, P_dn_above, optimize=True)
+    return np.einsum("ac,arRb,eb->crRe", P_up_below, X, P_dn_above, optimize=PAIRWISE)
 
 
 def normalise(t):
@@ -230,6 +237,36 @@ def corner_spectra(envs):
             row.append(s / np.sum(s))
         out.append(row)
     return np.array(out)
+
+
+def loop_spectra(envs, Lx=2, Ly=2):
+    """Gauge-invariant corner spectra, shape [sites, chi].
+
+    For the 2x2 block whose bottom-left site is i = (x, y), the four corners
+    around it joined directly, L = C1(x, y+1) C2(x+1, y+1) C3(x+1, y) C4(x, y),
+    close a loop: each corner leg meets the leg of its neighbour across the
+    same chi bond (the network with no edge tensors and no sites, whose
+    trace is the Z_00 of the free-energy ratio).  A change of basis G on any
+    chi bond turns L into a similar matrix, so its eigenvalues do not depend
+    on the gauge the projectors leave on the chi bonds, while the singular
+    values of a single corner do.  Returned: the eigenvalue moduli, sorted
+    descending, divided by their sum."""
+    out = []
+    for i in range(Lx * Ly):
+        x, y = i % Lx, i // Lx
+        L = (envs[_site(x, y + 1, Lx, Ly)]["C1"] @ envs[_site(x + 1, y + 1, Lx, Ly)]["C2"]
+             @ envs[_site(x + 1, y, Lx, Ly)]["C3"] @ envs[_site(x, y, Lx, Ly)]["C4"])
+        m = np.sort(np.abs(np.linalg.eigvals(L)))[::-1]
+        out.append(m / np.sum(m))
+    return np.array(out)
+
+
+def cut_singular_values(envs, As, x, y, Lx=2, Ly=2):
+    """All singular values of M = H_u^T H_d for the cut between rows y and
+    y+1 at column x (left move, unrotated lattice): the gap at chi tells
+    whether the truncation to chi is well posed."""
+    Hu, Hd = half_systems(*cut_corners(envs, As, x, y, Lx, Ly))
+    return np.linalg.svd(Hu.T @ Hd, compute_uv=False)
 
 
 def run(As, envs, chi, max_sweeps, tol=0.0, Lx=2, Ly=2, cutoff=1e-12):
@@ -376,9 +413,9 @@ def log_kappa_per_site(envs, As):
     t4a, t4b = E[BL]["T4"], E[TL]["T4"]
     z00 = np.einsum("ab,bc,cd,da->", c1, c2, c3, c4)
     z20 = np.einsum("ab,buUc,cvVe,ef,fg,gvVh,huUk,ka->",
-                    c1, t1a, t1b, c2, c3, t3a, t3b, c4, optimize=True)
+                    c1, t1a, t1b, c2, c3, t3a, t3b, c4, optimize=PAIRWISE)
     z02 = np.einsum("ab,bc,crRd,dsSe,ef,fg,gsSh,hrRa->",
-                    c1, c2, t2a, t2b, c3, c4, t4a, t4b, optimize=True)
+                    c1, c2, t2a, t2b, c3, c4, t4a, t4b, optimize=PAIRWISE)
     # upper half: C1 T1(TL) T1(TR) C2 T2(TR), the TR and TL sites, T4(TL)
     up = np.einsum("ab,buUc->auUc", c1, t1a)
     up = np.einsum("auUc,cvVe->auUvVe", up, t1b)

@@ -99,6 +99,33 @@ def ising_peps_tensor(beta: float):
     return np.ascontiguousarray(A)
 
 
+def gauged_ising_tensors(beta: float, seed: int, strength: float = 0.5):
+    """The Ising PEPS tensor on all four sites of the 2x2 cell, with an
+    independent random invertible matrix G = 1 + strength N(0,1) (seed) on
+    each of the 8 bonds: the source site's leg toward the bond gets G, the
+    target site's leg G^-1 (bonds in SQUARE_2X2_BONDS order; horizontal
+    bonds join r of the source to l of the target, vertical ones u of the
+    source to d of the target).  Contracting any bond gives back G G^-1 = 1
+    in ket and bra alike, so the norm network -- and every observable and
+    the free energy -- is the Ising model's at K = beta, while the four site
+    tensors all differ."""
+    rng = np.random.default_rng(seed)
+    A = ising_peps_tensor(beta)
+    As = [A.copy() for _ in range(4)]
+    for (i, dx, dy) in SQUARE_2X2_BONDS:
+        x, y = i % 2, i // 2
+        j = site_index(x + dx, y + dy)
+        G = np.eye(2) + strength * rng.standard_normal((2, 2))
+        Gi = np.linalg.inv(G)
+        if dx == 1:
+            As[i] = np.einsum("slurd,rk->slukd", As[i], G)
+            As[j] = np.einsum("kl,slurd->skurd", Gi, As[j])
+        else:
+            As[i] = np.einsum("slurd,uk->slkrd", As[i], G)
+            As[j] = np.einsum("kd,slurd->slurk", Gi, As[j])
+    return [np.ascontiguousarray(a) for a in As]
+
+
 # --------------------------------------------------------------------------
 # environments
 # --------------------------------------------------------------------------

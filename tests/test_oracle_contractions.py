@@ -218,3 +218,25 @@ def test_rotation_maps_vertical_to_horizontal(state):
     rv = R.rdm2(envs, As, i, 0, 1)
     rh = R.rdm2(e2, a2, 1, 1, 0)   # site 1 (image of j) left of site 0 (image of i)
     np.testing.assert_allclose(rv, R.swap_sites(rh, d, d), rtol=1e-11, atol=1e-13)
+
+
+def test_loop_spectra_vs_network(state):
+    """loop_spectra: the corner loop of each 2x2 block, built here from the
+    grid geometry with the closing bond left open, has the same eigenvalue
+    moduli."""
+    As, envs = state
+    for i in range(4):
+        x, y = i % 2, i // 2
+        net = NL.corners_only(envs, x, x + 1, y, y + 1)
+        net[3] = (net[3][0], [("B",), ("L'",)])      # open the bond C4 -> C1
+        L = NL.contract(net, [("L",), ("L'",)])
+        m = np.sort(np.abs(np.linalg.eigvals(L)))[::-1]
+        np.testing.assert_allclose(R.loop_spectra(envs)[i], m / m.sum(), rtol=1e-10, atol=1e-14)
+
+
+def test_test_side_loop_spectra_match_oracle(state):
+    """The tests' own loop-spectrum helper (applied to GPU environments)
+    computes the oracle's definition."""
+    import invariants as INV
+    As, envs = state
+    np.testing.assert_allclose(INV.loop_spectra(envs), R.loop_spectra(envs), rtol=1e-12, atol=1e-15)

@@ -218,3 +218,147 @@ def test_bond_list_golden():
     rows = [tuple(int(v) for v in l.split()) for l in open(os.path.join(GOLDEN, "square_2x2_bonds.txt"))
             if l.strip() and not l.startswith("#")]
     assert tuple(rows) == I.SQUARE_2X2_BONDS
+
+
+@pytest.fixture(scope="module", params=[0.6, 0.3])
+def gauged_ising(request):
+    beta = request.param
+    As = I.gauged_ising_tensors(beta, seed=7, strength=0.3)
+    envs = I.random_env(8, [2] * 4, seed=5)
+    envs, n, delta = R.run(As, envs, 8, 70)
+    return beta, As, envs
+
+
+def test_gauged_ising_sites_differ(gauged_ising):
+    _, As, _ = gauged_ising
+    for i in range(4):
+        for j in range(i):
+            assert np.abs(As[i] - As[j]).max() > 0.1
+
+
+def test_gauged_ising_onsager(gauged_ising):
+    """Ising PEPS with an independent random gauge on each of the 8 bonds:
+    the four sites differ, so each row cut has its own projectors and a
+    mixed-up cut index (which cut's P_up or P_dn feeds which absorbed
+    tensor) or site relabelling no longer cancels, while the network -- and
+    so <sigma^z>, <sigma sigma> on every bond and ln kappa -- is still the
+    Ising model's (Onsager, Yang)."""
+    beta, As, envs = gauged_ising
+    sz = np.diag([1.0, -1.0])
+    m = np.array([R.expect(sz, R.rdm1(envs, As, i)) for i in range(4)])
+    c = np.array([R.expect(np.kron(sz, sz), R.rdm2(envs, As, i, dx, dy)) for (i, dx, dy) in I.SQUARE_2X2_BONDS])
+    lk, sign = R.log_kappa_per_site(envs, As)
+    assert sign > 0
+    np.testing.assert_allclose(np.abs(m), X.yang_magnetisation(beta), atol=1e-9)
+    np.testing.assert_allclose(c, X.onsager_nn_correlation(beta), rtol=1e-9)
+    np.testing.assert_allclose(lk, X.onsager_log_z_per_site(beta), rtol=1e-10)
+
+
+def chi_bond_gauge(envs, chi, seed, strength=0.3):
+    """Apply an independent random invertible G to each of the 16 chi bonds
+    of a 2x2 cell's environment, consistently: the legs on one side of a
+    bond get G, those on the other side G^-1, so that every contraction of
+    the infinite network is unchanged.  The bonds follow from the geometry:
+      top of row y, between columns x and x+1: T1(x,y).c_C2 and C1(x+1,y).c_T1
+        on the left; T1(x+1,y).c_C1 and C2(x,y).c_T1 on the right;
+      right of column x, between rows y and y+1: T2(x,y+1).c_C3 and
+        C2(x,y).c_T2 above; T2(x,y).c_C2 and C3(x,y+1).c_T2 below;
+      bottom of row y: T3(x,y).c_C3 and C4(x+1,y).c_T3 left; T3(x+1,y).c_C4
+        and C3(x,y).c_T3 right;
+      left of column x: T4(x,y+1).c_C4 and C1(x,y).c_T4 above; T4(x,y).c_C1
+        and C4(x,y+1).c_T4 below."""
+    rng = np.random.default_rng(seed)
+    out = [{k: v.copy() for k, v in e.items()} for e in envs]
+    st = lambda x, y: I.site_index(x, y)
+
+    def on_leg(site, name, axis, M):
+        out[site][name] = np.moveaxis(np.tensordot(out[site][name], M, axes=([axis], [0])), -1, axis)
+
+    for a in range(2):
+        for b in range(2):
+            for kind in ("top", "right", "bot", "left"):
+                G = np.eye(chi) + strength * rng.standard_normal((chi, chi))
+                Gi = np.linalg.inv(G).T
+                if kind == "top":        # y = a, between x = b and b+1
+                    y, x = a, b
+                    one = [(st(x, y), "T1", 3), (st(x + 1, y), "C1", 1)]
+                    two = [(st(x + 1, y), "T1", 0), (st(x, y), "C2", 0)]
+                elif kind == "right":    # x = a, between y = b and b+1
+                    x, y = a, b
+                    one = [(st(x, y + 1), "T2", 3), (st(x, y), "C2", 1)]
+                    two = [(st(x, y), "T2", 0), (st(x, y + 1), "C3", 0)]
+                elif kind == "bot":
+                    y, x = a, b
+                    one = [(st(x, y), "T3", 0), (st(x + 1, y), "C4", 0)]
+                    two = [(st(x + 1, y), "T3", 3), (st(x, y), "C3", 1)]
+                else:
+                    x, y = a, b
+                    one = [(st(x, y + 1), "T4", 0), (st(x, y), "C1", 0)]
+                    two = [(st(x, y), "T4", 3), (st(x, y + 1), "C4", 1)]
+                for (i, n, ax) in one:
+                    on_leg(i, n, ax, G)
+                for (i, n, ax) in two:
+                    on_leg(i, n, ax, Gi)
+    return out
+
+
+@pytest.mark.parametrize("converged_env", [False, True])
+def test_chi_bond_gauge_invariants(converged, converged_env):
+    """Under a consistent random gauge of every chi bond the reduced density
+    matrices, the loop spectra and ln kappa are unchanged to rounding (for
+    any environment, converged or not), while the singular values of the
+    individual corners change at O(1).  So corner spectra are not gauge
+    invariant: two correct implementations whose projectors leave
+    different non-orthogonal gauges on the chi bonds give different corner
+    spectra, and the loop spectra are the gauge-invariant quantity to
+    compare.  A site mix-up in any RDM network joins legs of two different
+    bonds and breaks this invariance."""
+    As, envs, chi, _ = converged
+    if not converged_env:
+        envs = I.random_env(chi, [2] * 4, seed=21, per_site=True)
+    g = chi_bond_gauge(envs, chi, seed=3)
+    for i in range(4):
+        np.testing.assert_allclose(R.rdm1(g, As, i), R.rdm1(envs, As, i), rtol=1e-9, atol=1e-12)
+    for (i, dx, dy) in I.SQUARE_2X2_BONDS + ((1, -1, 0), (2, 0, -1)):
+        np.testing.assert_allclose(R.rdm2(g, As, i, dx, dy), R.rdm2(envs, As, i, dx, dy), rtol=1e-9, atol=1e-12)
+    np.testing.assert_allclose(R.loop_spectra(g), R.loop_spectra(envs), rtol=1e-8, atol=1e-12)
+    np.testing.assert_allclose(R.log_kappa_per_site(g, As)[0], R.log_kappa_per_site(envs, As)[0], rtol=1e-10)
+    assert np.max(np.abs(R.corner_spectra(g) - R.corner_spectra(envs))) > 1e-2
+
+
+def test_regauged_projectors_change_corner_spectra_not_invariants(monkeypatch):
+    """A CTMRG whose every projector pair is re-gauged, P_up -> P_up G and
+    P_dn -> G^-1 P_dn (random invertible G per cut and sweep), keeps
+    P_dn P_up = 1 and the kept subspace of each cut.  A non-orthogonal G on
+    the chi legs crossing the next cut changes that cut's M, so the fixed
+    point moves, but only at the truncation error (~1e-7 here), while the
+    individual corner spectra differ at O(1e-2)."""
+    As = I.neel_tensors(2, 2, 0.3, seed=4)
+    chi = 12
+    envs0 = I.random_env(chi, [2] * 4, seed=9)
+    plain, _, _ = R.run(As, envs0, chi, 60)
+    orig = R.projectors
+    rng = np.random.default_rng(17)
+
+    def regauged(*args, **kw):
+        P_up, P_dn, s = orig(*args, **kw)
+        G = np.eye(chi) + 0.3 * rng.standard_normal((chi, chi))
+        return P_up @ G, np.linalg.solve(G, P_dn), s
+
+    monkeypatch.setattr(R, "projectors", regauged)
+    scrambled, _, _ = R.run(As, envs0, chi, 60)
+    monkeypatch.setattr(R, "projectors", orig)
+    np.testing.assert_allclose(_observables(As, scrambled), _observables(As, plain), atol=1e-6)
+    np.testing.assert_allclose(R.loop_spectra(scrambled), R.loop_spectra(plain), atol=1e-6)
+    assert np.max(np.abs(R.corner_spectra(scrambled) - R.corner_spectra(plain))) > 1e-3
+
+
+def test_loop_spectrum_of_product_state():
+    """A product state's converged environment has rank one: one loop
+    eigenvalue.  (The chi space power-iterates with the edges' (0, 0) block,
+    so the rank-one limit is reached geometrically; 20 sweeps suffice.)"""
+    As = I.neel_tensors(2, 3, 0.0, seed=0)
+    envs, _, _ = R.run(As, I.random_env(5, [3] * 4, seed=1), 5, 20)
+    L = R.loop_spectra(envs)
+    np.testing.assert_allclose(L[:, 0], 1.0, atol=1e-12)
+    assert np.max(L[:, 1:]) < 1e-12
