@@ -96,13 +96,19 @@ typedef struct {
  * exact_svd_max_n=256, rsvd_warm_start=1. */
 ctm_status ctm_default_options(ctm_options* opt);
 
-/* Device bytes a handle of this shape allocates (workspace included). */
+/* Device bytes a handle of this shape allocates (workspace included): the
+ * environment of Sec. 2.2 (4 corners chi x chi, 4 edges chi x D x D x chi per
+ * site), the four enlarged corners of a cut (N x N, N = chi D^2) and the
+ * scratch of the projector and measurement steps.  No device work. */
 ctm_status ctm_footprint_bytes(int d, int D, const ctm_options* opt, size_t* bytes);
 
-/* Create a handle for a 2x2 cell with physical dim d and bond dim D on
- * the current CUDA device.  stream: a cudaStream_t, or NULL to create one
- * owned by the handle.  Allocates all device memory up front. */
-ctm_status ctm_create(int d, int D, const ctm_options* opt, void* stream, ctm_handle* out);
+/* Create a handle for an Lx x Ly unit cell of iTPS tensors (Sec. 2.1, the
+ * L_sub of Sec. 5.2) with physical dimension d and bond dimension D, on the
+ * current CUDA device.  Only Lx = Ly = 2 is built; other cells return
+ * CTM_ERR_ARG.  stream: a cudaStream_t, or NULL to create one owned by the
+ * handle.  Allocates all device memory up front (CTM_ERR_OOM if it does not
+ * fit); *out is NULL on any error, with the message in ctm_last_error(NULL). */
+ctm_status ctm_create(int Lx, int Ly, int d, int D, const ctm_options* opt, void* stream, ctm_handle* out);
 ctm_status ctm_destroy(ctm_handle h);
 
 /* Copy in the site tensor A of site i (d*D^4 doubles, C-order [s,l,u,r,d]). */
@@ -112,7 +118,17 @@ ctm_status ctm_set_tensor(ctm_handle h, int site, const double* A, int on_device
 ctm_status ctm_set_env(ctm_handle h, int site, int which, const double* t, int on_device);
 ctm_status ctm_get_env(ctm_handle h, int site, int which, double* t, int on_device);
 
-/* n CTMRG sweeps (left, top, right, bottom moves; Sec. 2.2). */
+/* Random initial environment (Sec. 2.2 starts CTMRG from an arbitrary
+ * environment): every C and T filled with standard normal numbers from the
+ * library's counter-based generator (Philox4x32-10, this seed), each T
+ * symmetrised over its ket/bra legs (k, k'), one draw shared by the four
+ * sites.  An alternative to ctm_set_env; the numbers differ from any host
+ * generator's.  Resets the range finder's warm start. */
+ctm_status ctm_init_env_random(ctm_handle h, uint64_t seed);
+
+/* n CTMRG sweeps (left, top, right, bottom moves; Sec. 2.2).  Returns
+ * CTM_NOT_CONVERGED (a status, not an error) when a projector SVD reached
+ * its Jacobi sweep cap during these sweeps. */
 ctm_status ctm_sweep(ctm_handle h, int n);
 
 /* Sweeps until the normalised corner spectra change by less than opt.tol
@@ -151,14 +167,29 @@ ctm_status ctm_spectrum_delta(ctm_handle h, double* delta);
 /* Normalised singular values (sum 1) of every corner: out[site][corner][chi]. */
 ctm_status ctm_corner_spectra(ctm_handle h, double* out_host);
 
-/* Reduced density matrices (host outputs, trace 1, rho[ket][bra]).
- * rdm2: target = site + (dx,dy), |dx|+|dy| == 1; rho over (source, target). */
+/* Reduced density matrices of the converged network (Sec. 5.3, the
+ * one-site and two-site observables; the network of Sec. 2.2 with the
+ * physical legs of the measured sites left open).  Host outputs, trace 1,
+ * rho[ket][bra]: rdm1 is d x d; rdm2 is d^2 x d^2 over (source, target) with
+ * target = site + (dx, dy), |dx| + |dy| == 1 (else CTM_ERR_ARG).
+ * Synchronises the handle's stream. */
 ctm_status ctm_rdm1(ctm_handle h, int site, double* rho_host);
 ctm_status ctm_rdm2(ctm_handle h, int site, int dx, int dy, double* rho_host);
 
-/* <O> = Tr(O rho) for a d*d (one-site) or d^2*d^2 (two-site) host operator. */
+/* <O> = Tr(O rho) (Sec. 5.3) for a real row-major host operator O[after]
+ * [before]: d x d for measure1, d^2 x d^2 on (source, target) for measure2. */
 ctm_status ctm_measure1(ctm_handle h, int site, const double* op, double* value);
 ctm_status ctm_measure2(ctm_handle h, int site, int dx, int dy, const double* op, double* value);
+
+/* ln kappa per site: the logarithm of the norm-network value per site
+ * (Sec. 2.2), -beta f for a classical network such as the 2D Ising model,
+ * from the 2x2 block ratio kappa_block = Z_22 Z_00 / (Z_20 Z_02): Z_22 the
+ * block with its full environment, Z_00 the four corners joined directly,
+ * Z_20 and Z_02 the row and column strips of edge tensors without sites.
+ * ln kappa = ln(kappa_block) / 4, for the site tensors as given (A -> c A
+ * adds 2 ln c).  CTM_ERR_NONFINITE when the ratio is not positive and
+ * finite.  Uses the handle's precision for its contractions. */
+ctm_status ctm_log_norm_per_site(ctm_handle h, double* lnkappa);
 
 /* Operator from the element format of Sec. 5.2: n lines of
  * (i_before, j_before, i_after, j_after) in idx[4n] and real parts re[n];
@@ -197,6 +228,15 @@ ctm_status ctm_profile_report(ctm_handle h, char* buf, size_t len, int reset);
  * and kernel-level calls); cudaMemset/cudaMemcpy are not counted. */
 long long ctm_kernel_launches(void);
 
+/* Failure-detection check (no counterpart in the paper): launches one
+ * thread that waits on an mbarrier with the same bounded wait the
+ * tensor-core GEMM uses, for at most limit_cycles (1 .. 4e9) SM clock
+ * cycles.  With arrive != 0 another thread arrives and the wait completes
+ * (CTM_OK); with arrive == 0 nothing arrives, the wait gives up and the call
+ * returns CTM_ERR_TIMEOUT with the context still usable.  flag_dev: one
+ * device int of scratch, owned by the caller.  Synchronises `stream`. */
+ctm_status ctm_wait_probe(long long limit_cycles, int arrive, int* flag_dev, void* stream);
+
 /* ------------------------------------------------------------------------
  * Kernel-level entry points.  All pointers are device pointers, work is
  * ordered on `stream` (cudaStream_t, NULL = legacy default stream), nothing
@@ -223,7 +263,9 @@ ctm_status ctm_qr(const double* Y, int N, int k, double* Q, double* R, void* ws,
 
 /* SVD of a small square G (k x k row-major, k <= 1024) by one-sided Jacobi:
  * G = U diag(S) V^T, S descending, U and V k x k row-major.  Columns of U
- * with S = 0 are zero.  ws: ctm_svd_workspace_bytes(k) bytes. */
+ * with S = 0 are zero.  ws: ctm_svd_workspace_bytes(k) bytes; its first int
+ * is set to 1 when the rotations had not settled after the sweep cap (the
+ * outputs are then the last iterate), else 0.  Not synchronised. */
 size_t ctm_svd_workspace_bytes(int k);
 ctm_status ctm_svd(const double* G, int k, double* U, double* S, double* V, void* ws,
                    void* stream);

@@ -20,6 +20,7 @@
 #include <algorithm>
 #include <array>
 #include <map>
+#include <mutex>
 #include <set>
 #include <cmath>
 #include <cstdio>
@@ -71,6 +72,7 @@ struct ctm_ctx {
     bool have_A[4] = {false, false, false, false};
     unsigned env_set = 0;  // bit (site*8 + which)
     uint64_t rng_counter = 0;
+    long long jacobi_capped = 0;  // read_flag calls that saw a capped Jacobi SVD
 
     std::vector<void*> allocs;
     double* A[4][4] = {};     // [site][rotation]  [s,l,u,r,d]
@@ -118,6 +120,8 @@ struct ctm_ctx {
     void* sval_ws = nullptr;
     unsigned long long* maxbits = nullptr;
     int* flag = nullptr;
+    double* dotws = nullptr;   // partial sums of ctm::dot
+    double* scal = nullptr;    // scalar results
 };
 
 namespace {
@@ -206,6 +210,7 @@ size_t footprint(int d, int D, const ctm_options& o) {
     size_t bytes = dbl * sizeof(double);
     bytes += qr_ws_bytes(N, k) + svd_ws_bytes(k) + svals_ws_bytes(chi, 16);
     bytes += 64 * sizeof(unsigned long long) + 64 + 64 * 256;
+    bytes += sizeof(double) * (ctm::dot_ws_doubles() + 8);
     if (o.precision == CTM_OZAKI_BF16) {
         const OzBounds z = oz_bounds(d, D, chi, k, o.ozaki_slices);
         bytes += z.a + z.b + z.w + 3 * 256 + 8 * ctm::oz_split_bytes(N, N, o.ozaki_slices);
@@ -259,7 +264,9 @@ struct ProfTag {
     ctm_ctx* h;
     const char* prev;
     ProfTag(ctm_ctx* h_, const char* t) : h(h_), prev(h_->tag) {
+        static std::mutex mu;
         static std::set<std::string> names;  // interned: records keep the pointer
+        std::lock_guard<std::mutex> lock(mu);
         h->tag = names.insert(t).first->c_str();
     }
     ~ProfTag() { h->tag = prev; }
@@ -393,7 +400,7 @@ ctm_status qr_(ctm_ctx* h, const double* Y, double* Q, double* R) {
 ctm_status svd_(ctm_ctx* h) {
     ProfTag tg(h, "svd");
     const size_t ev = prof_begin(h);
-    CK(ctm::svd(h->G, h->k, h->Us, h->Sv, h->Ws, h->svd_ws, h->stream));
+    CK(ctm::svd(h->G, h->k, h->Us, h->Sv, h->Ws, h->svd_ws, h->stream, h->flag + 2));
     prof_end(h, ev, P_SVD, 0.0, 0.0);
     return CTM_OK;
 }
@@ -631,9 +638,13 @@ ctm_status check_ready(ctm_ctx* h) {
 }
 
 ctm_status read_flag(ctm_ctx* h) {
-    int f[2] = {0, 0};
-    CK(cudaMemcpyAsync(f, h->flag, 2 * sizeof(int), cudaMemcpyDeviceToHost, h->stream));
+    int f[3] = {0, 0, 0};
+    CK(cudaMemcpyAsync(f, h->flag, 3 * sizeof(int), cudaMemcpyDeviceToHost, h->stream));
     CK(cudaStreamSynchronize(h->stream));
+    if (f[2]) {  // a projector SVD hit the Jacobi sweep cap: counted, not an error
+        ++h->jacobi_capped;
+        CK(cudaMemsetAsync(h->flag + 2, 0, sizeof(int), h->stream));
+    }
     if (f[1]) {
         h->err = "a bounded wait inside a tensor-core GEMM gave up";
         return CTM_ERR_TIMEOUT;
@@ -751,6 +762,76 @@ ctm_status rdm2_any(ctm_ctx* h, int site, int dx, int dy, std::vector<double>& r
     return CTM_OK;
 }
 
+// sum_i x[i] y[i] (device arrays) to the host
+ctm_status dot_host(ctm_ctx* h, const double* x, const double* y, size_t n, double* out) {
+    CK(ctm::dot(x, y, n, h->scal, h->dotws, h->stream));
+    CK(cudaMemcpyAsync(out, h->scal, sizeof(double), cudaMemcpyDeviceToHost, h->stream));
+    CK(cudaStreamSynchronize(h->stream));
+    return CTM_OK;
+}
+
+// Closed strip of a 2x2 block with no sites: the corners cTL, cTR, cBR, cBL
+// around it and, between them, two pairs of edges facing each other across
+// the block, each edge's ket/bra legs joined to those of the edge opposite.
+// With (cTL, e1, e2, cTR) = (C1, T1(TL), T1(TR), C2) on top and
+// (cBR, e3, e4, cBL) = (C3, T3(BR), T3(BL), C4) below this is Z_20; with the
+// right and left columns fed in the same roles it is Z_02.
+//   top[a,(u,U),(v,V),f] = cTL[a,b] e1[b,(u,U),c] e2[c,(v,V),e] cTR[e,f]
+//   bot[f,(v,V),(u,U),a] = cBR[f,g] e3[g,(v,V),h] e4[h,(u,U),k] cBL[k,a]
+//   Z = sum top[a,u,U,v,V,f] bot[f,v,V,u,U,a]
+ctm_status strip_value(ctm_ctx* h, const double* cTL, const double* e1, const double* e2, const double* cTR,
+                       const double* cBR, const double* e3, const double* e4, const double* cBL, double* z) {
+    const int chi = h->chi, N = h->N, D = h->D;
+    const int ND2 = N * D * D;
+    CKS(gemm(h, false, false, chi, N, chi, cTL, chi, e1, N, h->X1, N));
+    CKS(gemm(h, false, false, N, N, chi, h->X1, chi, e2, N, h->E[0], N));
+    CKS(gemm(h, false, false, ND2, chi, chi, h->E[0], chi, cTR, chi, h->E[1], chi));
+    CKS(gemm(h, false, false, chi, N, chi, cBR, chi, e3, N, h->X1, N));
+    CKS(gemm(h, false, false, N, N, chi, h->X1, chi, e4, N, h->E[0], N));
+    CKS(gemm(h, false, false, ND2, chi, chi, h->E[0], chi, cBL, chi, h->E[2], chi));
+    CKS(perm(h, h->E[2], h->E[0], {chi, D, D, D, D, chi}, {5, 3, 4, 1, 2, 0}));
+    return dot_host(h, h->E[1], h->E[0], (size_t)N * N, z);
+}
+
+// ln kappa per site (Sec. 2.2 norm network): for the 2x2 block TL = 2,
+// TR = 3, BL = 0, BR = 1, kappa_block = Z_22 Z_00 / (Z_20 Z_02) where Z_22 is
+// the block with its full environment (= Tr(H_u^T H_d) of the cut through
+// it), Z_00 the four corners joined directly, Z_20 / Z_02 the row / column
+// strips without sites; ln kappa per site = ln(kappa_block) / 4.  Every
+// environment normalisation cancels in the ratio.
+ctm_status log_norm_per_site(ctm_ctx* h, double* out) {
+    const int chi = h->chi, N = h->N;
+    const int TL = 2, TR = 3, BR = 1, BL = 0;
+    double z00 = 0, z20 = 0, z02 = 0, z22 = 0;
+    // Z_00 = Tr(C1 C2 C3 C4) = sum P[a,b] Q[b,a], P = C1 C2, Q = C3 C4
+    CKS(gemm(h, false, false, chi, chi, chi, h->env[TL][C1], chi, h->env[TR][C2], chi, h->newC1, chi));
+    CKS(gemm(h, false, false, chi, chi, chi, h->env[BR][C3], chi, h->env[BL][C4], chi, h->newC4, chi));
+    CKS(perm(h, h->newC4, h->corners, {chi, chi}, {1, 0}));
+    CKS(dot_host(h, h->newC1, h->corners, (size_t)chi * chi, &z00));
+    CKS(strip_value(h, h->env[TL][C1], h->env[TL][T1], h->env[TR][T1], h->env[TR][C2], h->env[BR][C3],
+                    h->env[BR][T3], h->env[BL][T3], h->env[BL][C4], &z20));
+    // columns: right (C2, T2(TR), T2(BR), C3) and left (C4, T4(BL), T4(TL), C1)
+    CKS(strip_value(h, h->env[TR][C2], h->env[TR][T2], h->env[BR][T2], h->env[BR][C3], h->env[BL][C4],
+                    h->env[BL][T4], h->env[TL][T4], h->env[TL][C1], &z02));
+    // Z_22 = sum (E_ul E_ur) o (E_bl E_br) over the cut between rows 0 and 1 at column 0
+    CKS(enlarged_corner(h, TL, 0, h->E[0]));
+    CKS(enlarged_corner(h, TR, 1, h->E[1]));
+    CKS(enlarged_corner(h, BR, 2, h->E[2]));
+    CKS(enlarged_corner(h, BL, 3, h->E[3]));
+    CKS(gemm(h, false, false, N, N, N, h->E[0], N, h->E[1], N, h->S1, N));
+    CKS(gemm(h, false, false, N, N, N, h->E[3], N, h->E[2], N, h->S3, N));
+    CKS(dot_host(h, h->S1, h->S3, (size_t)N * N, &z22));
+    const double ratio = z22 * z00 / (z20 * z02);
+    if (!(ratio > 0.0) || !std::isfinite(ratio)) {
+        char buf[200];
+        snprintf(buf, sizeof(buf), "ln kappa: Z22 Z00 / (Z20 Z02) = %.3e is not a positive finite number", ratio);
+        h->err = buf;
+        return CTM_ERR_NONFINITE;
+    }
+    *out = 0.25 * std::log(ratio);
+    return CTM_OK;
+}
+
 thread_local std::string g_err;
 
 }  // namespace
@@ -808,9 +889,13 @@ ctm_status ctm_footprint_bytes(int d, int D, const ctm_options* o, size_t* bytes
     return CTM_OK;
 }
 
-ctm_status ctm_create(int d, int D, const ctm_options* o, void* stream, ctm_handle* out) {
+ctm_status ctm_create(int Lx, int Ly, int d, int D, const ctm_options* o, void* stream, ctm_handle* out) {
     if (!out) return CTM_ERR_ARG;
     *out = nullptr;
+    if (Lx != 2 || Ly != 2) {
+        g_err = "ctm_create: only the 2x2 unit cell (Lx = Ly = 2) is built";
+        return CTM_ERR_ARG;
+    }
     if (validate(d, D, o) != CTM_OK) {
         g_err = "ctm_create: invalid dimensions or options";
         return CTM_ERR_ARG;
@@ -864,6 +949,8 @@ ctm_status ctm_create(int d, int D, const ctm_options* o, void* stream, ctm_hand
     if (st == CTM_OK) st = alloc(h, &h->sval_ws, svals_ws_bytes(h->chi, 16));
     if (st == CTM_OK) st = alloc(h, (void**)&h->maxbits, 64 * sizeof(unsigned long long));
     if (st == CTM_OK) st = alloc(h, (void**)&h->flag, 64);
+    if (st == CTM_OK) st = allocd(h, &h->dotws, ctm::dot_ws_doubles());
+    if (st == CTM_OK) st = allocd(h, &h->scal, 8);
     if (o->rsvd_warm_start && h->k < h->N)
         for (int c = 0; c < 16 && st == CTM_OK; ++c) st = allocd(h, &h->warmV[c], z.Nk);
     if (st == CTM_OK && o->precision == CTM_OZAKI_BF16) {
@@ -943,9 +1030,14 @@ ctm_status ctm_get_env(ctm_handle h, int site, int which, double* t, int on_devi
 ctm_status ctm_sweep(ctm_handle h, int n) {
     if (!h || n < 0) return CTM_ERR_ARG;
     CKS(check_ready(h));
+    const long long capped0 = h->jacobi_capped;
     for (int s = 0; s < n; ++s) CKS(one_sweep(h));
     const ctm_status st = read_flag(h);
     prof_collect(h);
+    if (st == CTM_OK && h->jacobi_capped > capped0) {
+        h->err = "a projector SVD reached the Jacobi sweep cap (results usable, rotations not fully converged)";
+        return CTM_NOT_CONVERGED;
+    }
     return st;
 }
 
@@ -1207,6 +1299,50 @@ ctm_status ctm_profile_read(ctm_handle h, ctm_profile_data* out, int reset) {
 }
 
 long long ctm_kernel_launches(void) { return ctm::g_launches; }
+
+ctm_status ctm_log_norm_per_site(ctm_handle h, double* lnkappa) {
+    if (!h || !lnkappa) return CTM_ERR_ARG;
+    CKS(check_ready(h));
+    CKS(log_norm_per_site(h, lnkappa));
+    return read_flag(h);
+}
+
+ctm_status ctm_init_env_random(ctm_handle h, uint64_t seed) {
+    if (!h) return CTM_ERR_ARG;
+    const size_t nC = (size_t)h->chi * h->chi, nT = (size_t)h->chi * h->D * h->D * h->chi;
+    for (int w = 0; w < 8; ++w) {
+        const size_t n = (w & 1) ? nT : nC;
+        CK(ctm::rng_normal(h->env[0][w], n, seed, 0x454e56ull * 16 + (uint64_t)w, h->stream));
+        if (w & 1) CK(ctm::sym_kk(h->env[0][w], h->chi, h->D, h->stream));
+        for (int i = 1; i < 4; ++i)
+            CK(cudaMemcpyAsync(h->env[i][w], h->env[0][w], n * sizeof(double), cudaMemcpyDeviceToDevice,
+                               h->stream));
+    }
+    CK(cudaStreamSynchronize(h->stream));
+    h->env_set = 0xffffffffu;
+    for (bool& w : h->warm_valid) w = false;
+    for (auto& c : h->ozc) c.valid = false;
+    return CTM_OK;
+}
+
+ctm_status ctm_wait_probe(long long limit_cycles, int arrive, int* flag_dev, void* stream) {
+    if (!flag_dev || limit_cycles <= 0 || limit_cycles > 4000000000ll) return CTM_ERR_ARG;
+    cudaStream_t st = (cudaStream_t)stream;
+    int f = 0;
+    cudaError_t e = cudaMemsetAsync(flag_dev, 0, sizeof(int), st);
+    if (e == cudaSuccess) e = ctm::wait_probe(limit_cycles, arrive, flag_dev, st);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(&f, flag_dev, sizeof(int), cudaMemcpyDeviceToHost, st);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+    if (e != cudaSuccess) {
+        g_err = std::string("ctm_wait_probe: ") + cudaGetErrorString(e);
+        return CTM_ERR_CUDA;
+    }
+    if (f) {
+        g_err = "ctm_wait_probe: the bounded wait gave up";
+        return CTM_ERR_TIMEOUT;
+    }
+    return CTM_OK;
+}
 
 ctm_status ctm_profile_report(ctm_handle h, char* buf, size_t len, int reset) {
     if (!h || !buf || len == 0) return CTM_ERR_ARG;

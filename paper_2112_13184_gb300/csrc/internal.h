@@ -2,6 +2,7 @@
 #pragma once
 
 #include <cuda_runtime.h>
+#include <atomic>
 #include <cstddef>
 #include <cstdint>
 
@@ -9,8 +10,9 @@
 
 namespace ctm {
 
-// kernel launches issued by this library (process-wide, all handles)
-extern long long g_launches;
+// kernel launches issued by this library (process-wide, all handles and
+// host threads)
+extern std::atomic<long long> g_launches;
 
 // ---- launch wrappers (kernels.cu) ----------------------------------------
 // All return cudaGetLastError() of their launch; work on `s`.
@@ -31,6 +33,11 @@ cudaError_t maxabs(const double* x, size_t n, unsigned long long* maxbits, cudaS
 // x /= max; sets *flag = 1 if max is not finite, 2 (when still 0) if max is 0
 cudaError_t scale_by_max(double* x, size_t n, const unsigned long long* maxbits, int* flag,
                          cudaStream_t s);
+// *out = sum_i x[i] y[i] in a fixed order; ws: dot_ws_doubles() doubles
+size_t dot_ws_doubles();
+cudaError_t dot(const double* x, const double* y, size_t n, double* out, double* ws, cudaStream_t s);
+// T[a,k,k',b] (chi x D x D x chi) symmetrised over (k, k') in place
+cudaError_t sym_kk(double* T, int chi, int D, cudaStream_t s);
 // out[i] = standard normal, Philox4x32-10 counter (seed, stream_id, i)
 cudaError_t rng_normal(double* out, size_t n, uint64_t seed, uint64_t stream_id, cudaStream_t s);
 
@@ -38,7 +45,10 @@ cudaError_t rng_normal(double* out, size_t n, uint64_t seed, uint64_t stream_id,
 size_t qr_ws_bytes(int N, int k);
 cudaError_t qr(const double* Y, int N, int k, double* Q, double* R, void* ws, cudaStream_t s);
 size_t svd_ws_bytes(int k);
-cudaError_t svd(const double* G, int k, double* U, double* S, double* V, void* ws, cudaStream_t s);
+// *status (optional; else the first int of ws) becomes 1 when the Jacobi
+// iteration still rotated in its last allowed sweep
+cudaError_t svd(const double* G, int k, double* U, double* S, double* V, void* ws, cudaStream_t s,
+                int* status = nullptr);
 // svd() with its workspace in a static device array (k <= svd_noalloc_max_k())
 int svd_noalloc_max_k();
 cudaError_t svd_noalloc(const double* G, int k, double* U, double* S, double* V, cudaStream_t s);
@@ -69,5 +79,10 @@ cudaError_t oz_gemm(int M, int N, int K, int s, const void* Asplit, const void* 
 cudaError_t oz_gemm_view(int M, int N, int K, int s, const void* Asplit, const void* Bsplit, double alpha,
                          double beta, double* C, const OzView& out_r, const OzView& out_c, void* ws, size_t ws_bytes,
                          int* err, cudaStream_t st);
+
+// Failure-detection check of the bounded mbarrier wait used by the tensor-core
+// GEMM: one thread waits at most limit_cycles on a barrier that receives an
+// arrival only when `arrive` is set; *err becomes 1 when the wait gave up.
+cudaError_t wait_probe(long long limit_cycles, int arrive, int* err, cudaStream_t st);
 
 }  // namespace ctm

@@ -8,7 +8,7 @@
 
 namespace ctm {
 
-long long g_launches = 0;
+std::atomic<long long> g_launches{0};
 
 // ---------------------------------------------------------------------------
 // FP64 GEMM, row-major: C[M,N] = alpha op(A) op(B) + beta C.
@@ -293,6 +293,50 @@ __global__ void k_rng_normal(double* __restrict__ out, size_t n, uint64_t seed, 
         if (2 * p + 1 < n) out[2 * p + 1] = rad * sn;
     }
 }
+// Dot product in two passes with a fixed grid, so the summation order (and
+// the result) does not depend on scheduling: pass 1 leaves one partial per
+// block, pass 2 (one block) adds them in block order.
+constexpr int DOT_BLOCKS = 152 * 4;
+__global__ void k_dot_partial(const double* __restrict__ x, const double* __restrict__ y, size_t n,
+                              double* __restrict__ part) {
+    double acc = 0.0;
+    for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x)
+        acc = fma(x[i], y[i], acc);
+    for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
+    __shared__ double sm[32];
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    if (lane == 0) sm[w] = acc;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        double t = 0.0;
+        for (int i = 0; i < (int)(blockDim.x >> 5); ++i) t += sm[i];
+        part[blockIdx.x] = t;
+    }
+}
+__global__ void k_dot_final(const double* __restrict__ part, int np, double* __restrict__ out) {
+    __shared__ double sm[256];
+    double t = 0.0;
+    for (int i = threadIdx.x; i < np; i += blockDim.x) t += part[i];
+    sm[threadIdx.x] = t;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        double s = 0.0;
+        for (int i = 0; i < (int)blockDim.x; ++i) s += sm[i];
+        *out = s;
+    }
+}
+// T[a,k,k',b] <- (T[a,k,k',b] + T[a,k',k,b]) / 2, one thread per pair k <= k'
+__global__ void k_sym_kk(double* __restrict__ T, int chi, int D) {
+    const size_t total = (size_t)chi * D * D * chi;
+    for (size_t t = blockIdx.x * (size_t)blockDim.x + threadIdx.x; t < total; t += (size_t)gridDim.x * blockDim.x) {
+        const size_t b = t % chi, kk2 = (t / chi) % D, kk = (t / ((size_t)chi * D)) % D, a = t / ((size_t)chi * D * D);
+        if (kk > kk2) continue;
+        const size_t i1 = ((a * D + kk) * D + kk2) * chi + b, i2 = ((a * D + kk2) * D + kk) * chi + b;
+        const double v = 0.5 * (T[i1] + T[i2]);
+        T[i1] = v;
+        T[i2] = v;
+    }
+}
 inline unsigned grid_for(size_t n, unsigned threads = 256) {
     size_t b = (n + threads - 1) / threads;
     if (b > 152 * 32) b = 152 * 32;
@@ -322,6 +366,19 @@ cudaError_t scale_by_max(double* x, size_t n, const unsigned long long* maxbits,
     if (!n) return cudaSuccess;
     ++g_launches;
     k_scale_by_max<<<grid_for(n), 256, 0, s>>>(x, n, maxbits, flag);
+    return cudaGetLastError();
+}
+size_t dot_ws_doubles() { return DOT_BLOCKS; }
+cudaError_t dot(const double* x, const double* y, size_t n, double* out, double* ws, cudaStream_t s) {
+    ++g_launches;
+    k_dot_partial<<<DOT_BLOCKS, 256, 0, s>>>(x, y, n, ws);
+    ++g_launches;
+    k_dot_final<<<1, 256, 0, s>>>(ws, DOT_BLOCKS, out);
+    return cudaGetLastError();
+}
+cudaError_t sym_kk(double* T, int chi, int D, cudaStream_t s) {
+    ++g_launches;
+    k_sym_kk<<<grid_for((size_t)chi * D * D * chi), 256, 0, s>>>(T, chi, D);
     return cudaGetLastError();
 }
 cudaError_t rng_normal(double* out, size_t n, uint64_t seed, uint64_t sid, cudaStream_t s) {

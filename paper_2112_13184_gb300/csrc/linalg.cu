@@ -181,7 +181,8 @@ __device__ __forceinline__ void cluster_sync() {
 __global__ void __launch_bounds__(256) k_jacobi_cluster(double* __restrict__ Gt, double* __restrict__ Wt, int k,
                                                        int n, int max_sweeps, double tol,
                                                        unsigned long long* __restrict__ off,
-                                                       double* __restrict__ nrm, int csize) {
+                                                       double* __restrict__ nrm, int csize,
+                                                       int* __restrict__ status) {
     constexpr int RK = 8;  // cached entries per lane: k <= 32 RK
     const int b = blockIdx.x / csize, rank = blockIdx.x % csize;
     const int warps = blockDim.x >> 5, lane = threadIdx.x & 31;
@@ -268,6 +269,8 @@ __global__ void __launch_bounds__(256) k_jacobi_cluster(double* __restrict__ Gt,
         const double o = __longlong_as_double((long long)__ldcg(offb + sw));
         cluster_sync();  // everyone has read this sweep's value before anyone moves on
         if (o < tol) break;
+        // the last sweep still rotated: report that the cap was hit
+        if (sw == max_sweeps - 1 && rank == 0 && threadIdx.x == 0 && status) atomicExch(status, 1);
     }
 }
 
@@ -331,6 +334,15 @@ __global__ void k_jacobi_round(double* __restrict__ Gt, double* __restrict__ Wt,
             wq[i] = sn * x + cs * y;
         }
     }
+}
+
+// after the per-round fallback: the cap was hit when the last sweep rotated
+__global__ void k_jacobi_status(const unsigned long long* __restrict__ off, int nb, int max_sweeps, double tol,
+                                int* __restrict__ status) {
+    for (int b = threadIdx.x; b < nb; b += blockDim.x)
+        if (!(__longlong_as_double((long long)off[(size_t)(max_sweeps - 1) * nb + b]) < tol) &&
+            off[(size_t)(max_sweeps - 1) * nb + b] != 0ull)
+            atomicExch(status, 1);
 }
 
 // sigma_c = |g_c|; rank = position in descending order (ties by index).
@@ -447,20 +459,51 @@ cudaError_t qr(const double* Y, int N, int k, double* Q, double* R, void* ws, cu
     return cudaGetLastError();
 }
 
-// Jacobi on nb matrices: one 16-CTA cluster per matrix when the device
-// allows it (8 otherwise), else one launch per round.
-cudaError_t jacobi(double* Gt, double* Wt, int k, int n, int nb, unsigned long long* off, double* nrm,
-                   cudaStream_t s) {
-    static int csize = -1;
-    if (csize < 0) {
-        csize = 0;
-        if (cudaFuncSetAttribute(k_jacobi_cluster, cudaFuncAttributeNonPortableClusterSizeAllowed, 1) == cudaSuccess)
-            csize = 16;
-        else
-            csize = 8;
+// Cluster size for the Jacobi kernel on the current device: 16 CTAs when the
+// device accepts that non-portable size, else 8, else 0 (per-round launches).
+// Decided once per device from occupancy queries, which launch nothing, so
+// the first call may come inside a stream capture.
+int jacobi_cluster_size() {
+    static std::mutex mu;
+    static int cached[64];
+    static unsigned long long known = 0;
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) return 0;
+    std::lock_guard<std::mutex> lock(mu);
+    if (known >> dev & 1ull) return cached[dev];
+    int cs = 0;
+    if (cudaFuncSetAttribute(k_jacobi_cluster, cudaFuncAttributeNonPortableClusterSizeAllowed, 1) != cudaSuccess)
+        cudaGetLastError();
+    for (int want : {16, 8}) {
+        cudaLaunchConfig_t cfg = {};
+        cfg.gridDim = dim3((unsigned)want, 1, 1);
+        cfg.blockDim = dim3(256, 1, 1);
+        cudaLaunchAttribute at[1];
+        at[0].id = cudaLaunchAttributeClusterDimension;
+        at[0].val.clusterDim.x = want;
+        at[0].val.clusterDim.y = 1;
+        at[0].val.clusterDim.z = 1;
+        cfg.attrs = at;
+        cfg.numAttrs = 1;
+        int nclusters = 0;
+        if (cudaOccupancyMaxActiveClusters(&nclusters, k_jacobi_cluster, &cfg) == cudaSuccess && nclusters > 0) {
+            cs = want;
+            break;
+        }
         cudaGetLastError();
     }
-    for (int attempt = 0; attempt < 2 && csize > 0; ++attempt) {
+    cached[dev] = cs;
+    known |= 1ull << dev;
+    return cs;
+}
+
+// Jacobi on nb matrices: one cluster per matrix when the device allows it,
+// else one launch per round.  *status (optional) becomes 1 when a matrix
+// still needed rotations in the last allowed sweep.
+cudaError_t jacobi(double* Gt, double* Wt, int k, int n, int nb, unsigned long long* off, double* nrm,
+                   int* status, cudaStream_t s) {
+    const int csize = jacobi_cluster_size();
+    if (csize > 0) {
         cudaLaunchConfig_t cfg = {};
         cfg.gridDim = dim3((unsigned)(nb * csize), 1, 1);
         cfg.blockDim = dim3(256, 1, 1);
@@ -474,41 +517,45 @@ cudaError_t jacobi(double* Gt, double* Wt, int k, int n, int nb, unsigned long l
         cfg.attrs = at;
         cfg.numAttrs = 1;
         ++g_launches;
-        const cudaError_t e = cudaLaunchKernelEx(&cfg, k_jacobi_cluster, Gt, Wt, k, n, JACOBI_MAX_SWEEPS,
-                                                 jacobi_tol(k), off, nrm, csize);
-        if (e == cudaSuccess) return cudaSuccess;
-        cudaGetLastError();
-        --g_launches;
-        csize = csize > 8 ? 8 : 0;  // retry with a portable cluster, then give up on clusters
+        return cudaLaunchKernelEx(&cfg, k_jacobi_cluster, Gt, Wt, k, n, JACOBI_MAX_SWEEPS, jacobi_tol(k), off, nrm,
+                                  csize, status);
     }
     for (int sw = 0; sw < JACOBI_MAX_SWEEPS; ++sw)
         for (int r = 0; r < n - 1; ++r) {
             ++g_launches;
             k_jacobi_round<<<dim3(n / 2, nb), 32, 0, s>>>(Gt, Wt, k, n, r, sw, off, jacobi_tol(k));
         }
+    if (status) {
+        ++g_launches;
+        k_jacobi_status<<<1, 256, 0, s>>>(off, nb, JACOBI_MAX_SWEEPS, jacobi_tol(k), status);
+    }
     return cudaGetLastError();
 }
 
-// scratch: G^T and W^T (k x k each), squared column norms (k), per-sweep
-// off-diagonal maxima
-size_t svd_ws_bytes(int k) {
-    return sizeof(double) * (2 * (size_t)k * k + k) + sizeof(unsigned long long) * JACOBI_MAX_SWEEPS + 256;
+// scratch: status word (256 bytes), G^T and W^T (k x k each), squared column
+// norms (k), per-sweep off-diagonal maxima
+constexpr size_t svd_ws_bytes_c(int k) {
+    return 256 + sizeof(double) * (2 * (size_t)k * k + k) + sizeof(unsigned long long) * JACOBI_MAX_SWEEPS + 256;
 }
+size_t svd_ws_bytes(int k) { return svd_ws_bytes_c(k); }
 
-cudaError_t svd(const double* G, int k, double* U, double* S, double* V, void* ws, cudaStream_t s) {
+cudaError_t svd(const double* G, int k, double* U, double* S, double* V, void* ws, cudaStream_t s, int* status) {
     if (k <= 0 || k > 1024) return cudaErrorInvalidValue;
-    double* Gt = (double*)ws;
+    int* st = (int*)ws;  // 1 if the Jacobi sweep cap was hit
+    double* Gt = (double*)((char*)ws + 256);
     double* Wt = Gt + (size_t)k * k;
     double* nrm = Wt + (size_t)k * k;
     unsigned long long* off = (unsigned long long*)(nrm + k);
     cudaError_t e = cudaMemsetAsync(off, 0, sizeof(unsigned long long) * JACOBI_MAX_SWEEPS, s);
+    if (e) return e;
+    e = cudaMemsetAsync(st, 0, sizeof(int), s);
     if (e) return e;
     ++g_launches;
     k_transpose_batch<<<grid_for((size_t)k * k), 256, 0, s>>>(G, Gt, k, 1);
     ++g_launches;
     k_eye_batch<<<grid_for((size_t)k * k), 256, 0, s>>>(Wt, k, 1);
     const int n = k + (k & 1);
-    e = jacobi(Gt, Wt, k, n, 1, off, nrm, s);
+    e = jacobi(Gt, Wt, k, n, 1, off, nrm, status ? status : st, s);
     if (e) return e;
     ++g_launches;
     k_jacobi_finish<<<1, 256, sizeof(double) * k, s>>>(Gt, Wt, k, U, S, V);
@@ -530,7 +577,7 @@ cudaError_t svals_normalised(const double* Gs, int k, int nb, double* out, void*
     ++g_launches;
     k_transpose_batch<<<grid_for((size_t)nb * k * k), 256, 0, s>>>(Gs, Gt, k, nb);
     const int n = k + (k & 1);
-    e = jacobi(Gt, nullptr, k, n, nb, off, nrm, s);
+    e = jacobi(Gt, nullptr, k, n, nb, off, nrm, nullptr, s);
     if (e) return e;
     ++g_launches;
     k_svals_finish<<<nb, 256, sizeof(double) * k, s>>>(Gt, k, out);
@@ -546,9 +593,7 @@ cudaError_t svals_normalised(const double* Gs, int k, int nb, double* out, void*
 // ---------------------------------------------------------------------------
 namespace {
 constexpr int SVD_NOALLOC_MAX_K = 256;
-constexpr size_t SVD_NOALLOC_BYTES =
-    sizeof(double) * (2 * (size_t)SVD_NOALLOC_MAX_K * SVD_NOALLOC_MAX_K + SVD_NOALLOC_MAX_K) +
-    sizeof(unsigned long long) * JACOBI_MAX_SWEEPS + 256;
+constexpr size_t SVD_NOALLOC_BYTES = svd_ws_bytes_c(SVD_NOALLOC_MAX_K);
 static __device__ __align__(256) unsigned char g_svd_scratch[SVD_NOALLOC_BYTES];
 
 constexpr int MAX_DEVICES = 64;
@@ -560,9 +605,8 @@ int svd_noalloc_max_k() { return SVD_NOALLOC_MAX_K; }
 
 cudaError_t svd_noalloc(const double* G, int k, double* U, double* S, double* V, cudaStream_t s) {
     if (k <= 0 || k > SVD_NOALLOC_MAX_K) return cudaErrorInvalidValue;
-    static_assert(SVD_NOALLOC_BYTES + 256 >= sizeof(double) * (2 * (size_t)SVD_NOALLOC_MAX_K * SVD_NOALLOC_MAX_K +
-                                                               SVD_NOALLOC_MAX_K) +
-                                                sizeof(unsigned long long) * JACOBI_MAX_SWEEPS + 256,
+    // every k accepted here needs at most the workspace of the largest k
+    static_assert(svd_ws_bytes_c(SVD_NOALLOC_MAX_K) <= sizeof(g_svd_scratch),
                   "scratch holds the Jacobi workspace of the largest k");
     int dev = 0;
     cudaError_t e = cudaGetDevice(&dev);
@@ -579,7 +623,7 @@ cudaError_t svd_noalloc(const double* G, int k, double* U, double* S, double* V,
         }
         ws = g_scratch_ptr[dev];
     }
-    return svd(G, k, U, S, V, ws, s);
+    return svd(G, k, U, S, V, ws, s, nullptr);
 }
 
 }  // namespace ctm

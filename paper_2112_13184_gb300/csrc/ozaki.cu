@@ -155,13 +155,29 @@ __device__ __forceinline__ long long f32_fixed(float f, int k) {
     return (b >> 31) ? -v : v;
 }
 
+// f 2^k as an int for an FP32 f whose f 2^k is a whole number below 2^31
+// (the level-0 and level-1 sums of one K chunk), by shifting the FP32
+// significand: integer instructions only, where a float-to-int conversion
+// would run on GB300's narrow FP64/conversion pipe.
+__device__ __forceinline__ int f32_exact_int(float f, int k) {
+    const unsigned b = __float_as_uint(f);
+    const int ex = (int)((b >> 23) & 0xff);
+    const unsigned mant = (b & 0x7fffffu) | 0x800000u;
+    const int sh = ex - 150 + k;  // |f| 2^k = mant 2^sh
+    unsigned v;
+    if (ex == 0 || sh <= -24) v = 0u;
+    else if (sh >= 0) v = sh < 8 ? mant << sh : 0x7fffffffu;  // >= 2^31: not a valid level sum
+    else v = mant >> (-sh);
+    return (b >> 31) ? -(int)v : (int)v;
+}
+
 // C = 2^(eA+eB-16) (S0 + S1/256 + F).  With T = 256 S0 + S1 (exact; |T| <
 // 2^39 for K <= 16384 per split) and F kept to 2^-28 of an S0 unit (below
 // 2^-44 of max|row| max|col|), Z = 2^20 T + round(2^28 F) is an exact int64
 // and C = Z 2^(eA+eB-44).  escale = eA + eB - 16.
 __device__ __forceinline__ double assemble(int S0, int S1, float F, int escale) {
     const long long T = (long long)S0 * 256 + (long long)S1;
-    const long long Z = T * (1ll << 20) + __float2ll_rn(F * 268435456.0f);  // F 2^28 < 2^62
+    const long long Z = T * (1ll << 20) + f32_fixed(F, 28);  // F 2^28 < 2^62
     return i64_ldexp(Z, escale - 28);
 }
 
@@ -496,18 +512,36 @@ __device__ __forceinline__ bool mbar_try_wait(uint64_t* bar, uint32_t parity) {
         : "memory");
     return ok != 0;
 }
-// Bounded wait: gives up after ~2e9 cycles, or at once when another thread
-// has already given up, recording the failure in *err.
-__device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity, int* err) {
+// Bounded wait: gives up after `limit` cycles (about 1 s at the default
+// 2e9), or at once when another thread has already given up, recording the
+// failure in *err.
+constexpr long long WAIT_LIMIT_CYCLES = 2000000000ll;
+__device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity, int* err,
+                                          long long limit = WAIT_LIMIT_CYCLES) {
     const long long t0 = clock64();
     while (!mbar_try_wait(bar, parity)) {
         if (*(volatile int*)err) return false;
-        if (clock64() - t0 > 2000000000ll) {
+        if (clock64() - t0 > limit) {
             atomicCAS(err, 0, 1);
             return false;
         }
     }
     return true;
+}
+
+// Failure-detection check of the bounded wait above: thread 0 waits on an
+// mbarrier of count 1.  With `arrive` set, thread 32 arrives on it (the wait
+// completes); without, nothing ever arrives and the wait must give up after
+// `limit` cycles, set *err and return, leaving the context usable.
+__global__ void k_wait_probe(long long limit, int arrive, int* err) {
+    __shared__ uint64_t bar;
+    if (threadIdx.x == 0) {
+        mbar_init(&bar, 1);
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    __syncthreads();
+    if (threadIdx.x == 32 && arrive) mbar_arrive(&bar);
+    if (threadIdx.x == 0) mbar_wait(&bar, 0u, err, limit);
 }
 
 __device__ __forceinline__ void tma_load_3d(void* dst, const CUtensorMap* map, int c0, int c1, int c2,
@@ -581,6 +615,7 @@ struct GemmArgs {
     int Mpad, Npad;
     int m_tiles, n_tiles;
     int* err;
+    long long wait_limit; // cycles before a bounded wait gives up
 };
 
 template <int NB16>
@@ -647,7 +682,7 @@ __global__ void __launch_bounds__(THREADS, 1)
                 for (int i = 0; i < nkb; ++i) {
                     const int st = issued % g.stages;
                     const uint32_t ph = (uint32_t)(issued / g.stages) & 1u;
-                    if (!mbar_wait(&empty[st], ph ^ 1u, g.err)) {
+                    if (!mbar_wait(&empty[st], ph ^ 1u, g.err, g.wait_limit)) {
                         ok = false;
                         break;
                     }
@@ -664,7 +699,7 @@ __global__ void __launch_bounds__(THREADS, 1)
                 for (int i = max(0, issued - g.stages); i < issued; ++i) {
                     const long long t0 = clock64();
                     while (!mbar_try_wait(&full[i % g.stages], (uint32_t)(i / g.stages) & 1u) &&
-                           clock64() - t0 < 2000000000ll) {
+                           clock64() - t0 < g.wait_limit) {
                     }
                 }
             }
@@ -682,11 +717,11 @@ __global__ void __launch_bounds__(THREADS, 1)
                 const uint32_t ph = (uint32_t)(it / g.stages) & 1u;
                 const bool first = (i % CHUNK_KB) == 0;
                 const bool last = (i % CHUNK_KB) == CHUNK_KB - 1 || i == nkb - 1;
-                if (first && cc > 0 && !mbar_wait(acc_empty, (uint32_t)(cc - 1) & 1u, g.err)) {
+                if (first && cc > 0 && !mbar_wait(acc_empty, (uint32_t)(cc - 1) & 1u, g.err, g.wait_limit)) {
                     ok = false;
                     break;
                 }
-                if (!mbar_wait(&full[st], ph, g.err)) {
+                if (!mbar_wait(&full[st], ph, g.err, g.wait_limit)) {
                     ok = false;
                     break;
                 }
@@ -715,7 +750,7 @@ __global__ void __launch_bounds__(THREADS, 1)
             // every MMA issued by this thread completes before TMEM is freed
             tc_commit(drain);
             const long long t0 = clock64();
-            while (!mbar_try_wait(drain, 0u) && clock64() - t0 < 2000000000ll) {
+            while (!mbar_try_wait(drain, 0u) && clock64() - t0 < g.wait_limit) {
             }
         }
     } else {
@@ -733,7 +768,7 @@ __global__ void __launch_bounds__(THREADS, 1)
 #pragma unroll
             for (int j = 0; j < 16; ++j) S0[jb][j] = S1[jb][j] = 0, F[jb][j] = 0.f;
         for (int c = 0; c < nchunks; ++c, ++cc) {
-            if (!mbar_wait(acc_full, (uint32_t)cc & 1u, g.err)) {
+            if (!mbar_wait(acc_full, (uint32_t)cc & 1u, g.err, g.wait_limit)) {
                 ok = false;
                 break;
             }
@@ -748,8 +783,8 @@ __global__ void __launch_bounds__(THREADS, 1)
                     tc_wait_ld();
 #pragma unroll
                     for (int j = 0; j < 16; ++j) {
-                        S0[jb][j] += __float2int_rn(__uint_as_float(r0[j]));
-                        S1[jb][j] += __float2int_rn(__uint_as_float(r1[j]) * 256.0f);
+                        S0[jb][j] += f32_exact_int(__uint_as_float(r0[j]), 0);
+                        S1[jb][j] += f32_exact_int(__uint_as_float(r1[j]), 8);
                     }
                     if (c == nchunks - 1 && g.s > 2) {
                         uint32_t r2[16];
@@ -913,19 +948,27 @@ Plan plan_of(int M, int N, int K, int s) {
 template <int NB16>
 cudaError_t launch_gemm(const Plan& p, const CUtensorMap& ta, const CUtensorMap& tb, const oz::GemmArgs& g,
                         cudaStream_t st) {
-    static bool attr = false;
-    if (!attr) {
-        cudaError_t e = cudaFuncSetAttribute(oz::k_oz_gemm<NB16>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                             227 * 1024);
-        if (e != cudaSuccess) return e;
-        attr = true;
+    // the 227 KB dynamic shared-memory opt-in is a per-device function
+    // attribute: set it once for every device this instantiation runs on
+    static std::mutex mu;
+    static unsigned long long done = 0;  // bit per device
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return e;
+    if (dev < 0 || dev >= 64) return cudaErrorInvalidDevice;
+    {
+        std::lock_guard<std::mutex> lock(mu);
+        if (!(done >> dev & 1ull)) {
+            e = cudaFuncSetAttribute(oz::k_oz_gemm<NB16>, cudaFuncAttributeMaxDynamicSharedMemorySize, 227 * 1024);
+            if (e != cudaSuccess) return e;
+            done |= 1ull << dev;
+        }
     }
     dim3 grid(p.m_tiles, p.n_tiles, p.ksplit);
     if (g.direct) {
         // persistent: one CTA per SM (the stage ring fills shared memory)
-        int dev = 0, nsm = 0;
-        cudaError_t e = cudaGetDevice(&dev);
-        if (e == cudaSuccess) e = cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
+        int nsm = 0;
+        e = cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
         if (e != cudaSuccess) return e;
         const long long tiles = (long long)p.m_tiles * p.n_tiles;
         grid = dim3((unsigned)std::min<long long>(tiles, nsm > 0 ? nsm : 1), 1, 1);
@@ -1030,6 +1073,12 @@ cudaError_t oz_split_view(const double* X, int R, int K, const OzView& rvh, cons
     return cudaGetLastError();
 }
 
+cudaError_t wait_probe(long long limit_cycles, int arrive, int* err, cudaStream_t st) {
+    ++g_launches;
+    oz::k_wait_probe<<<1, 64, 0, st>>>(limit_cycles, arrive, err);
+    return cudaGetLastError();
+}
+
 size_t oz_gemm_ws_bytes(int M, int N, int K, int s) { return plan_of(M, N, K, s).ws_bytes; }
 
 cudaError_t oz_gemm(int M, int N, int K, int s, const void* Asplit, const void* Bsplit, double alpha, double beta,
@@ -1083,6 +1132,7 @@ cudaError_t oz_gemm_view(int M, int N, int K, int s, const void* Asplit, const v
         g.PF = (float*)((char*)ws + 2 * part);
     }
     g.err = err;
+    g.wait_limit = oz::WAIT_LIMIT_CYCLES;
     cudaError_t e;
     switch (p.nb16) {
         case 1: e = launch_gemm<1>(p, ta, tb, g, st); break;

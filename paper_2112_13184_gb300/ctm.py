@@ -56,7 +56,8 @@ def _sig(name, res, *args):
 
 _sig("ctm_default_options", c_int, ctypes.POINTER(ctm_options))
 _sig("ctm_footprint_bytes", c_int, c_int, c_int, ctypes.POINTER(ctm_options), ctypes.POINTER(c_size_t))
-_sig("ctm_create", c_int, c_int, c_int, ctypes.POINTER(ctm_options), c_void_p, ctypes.POINTER(c_void_p))
+_sig("ctm_create", c_int, c_int, c_int, c_int, c_int, ctypes.POINTER(ctm_options), c_void_p,
+     ctypes.POINTER(c_void_p))
 _sig("ctm_destroy", c_int, c_void_p)
 _sig("ctm_set_tensor", c_int, c_void_p, c_int, c_void_p, c_int)
 _sig("ctm_set_env", c_int, c_void_p, c_int, c_int, c_void_p, c_int)
@@ -87,6 +88,9 @@ _sig("ctm_gemm_ozaki_workspace_bytes", c_size_t, c_int, c_int, c_int, c_int)
 _sig("ctm_gemm_ozaki", c_int, c_int, c_int, c_int, c_int, c_int, c_double, c_void_p, c_int, c_void_p, c_int,
      c_double, c_void_p, c_int, c_int, c_void_p, c_void_p)
 _sig("ctm_svd_noalloc", c_int, c_void_p, c_int, c_void_p, c_void_p, c_void_p, c_void_p)
+_sig("ctm_log_norm_per_site", c_int, c_void_p, c_dp)
+_sig("ctm_init_env_random", c_int, c_void_p, ctypes.c_uint64)
+_sig("ctm_wait_probe", c_int, ctypes.c_longlong, c_int, c_void_p, c_void_p)
 _sig("ctm_profile_enable", c_int, c_void_p, c_int)
 _sig("ctm_profile_read", c_int, c_void_p, ctypes.POINTER(ctm_profile_data), c_int)
 _sig("ctm_kernel_launches", ctypes.c_longlong)
@@ -103,7 +107,7 @@ class CtmError(RuntimeError):
 
 def _check(st, h=None):
     if st < 0:
-        msg = _lib.ctm_last_error(h).decode(errors="replace") if True else ""
+        msg = _lib.ctm_last_error(h).decode(errors="replace")
         raise CtmError(st, msg)
     return st
 
@@ -147,9 +151,9 @@ def ctm_footprint_bytes(d, D, opt: ctm_options) -> int:
     return b.value
 
 
-def ctm_create(d, D, opt: ctm_options, stream=None):
+def ctm_create(d, D, opt: ctm_options, stream=None, Lx=2, Ly=2):
     h = c_void_p()
-    _check(_lib.ctm_create(d, D, ctypes.byref(opt), _stream_ptr(stream), ctypes.byref(h)), None)
+    _check(_lib.ctm_create(Lx, Ly, d, D, ctypes.byref(opt), _stream_ptr(stream), ctypes.byref(h)), None)
     return h
 
 
@@ -205,6 +209,24 @@ def ctm_spectrum_delta(h):
     d = c_double()
     _check(_lib.ctm_spectrum_delta(h, ctypes.byref(d)), h)
     return d.value
+
+
+def ctm_log_norm_per_site(h):
+    v = c_double()
+    _check(_lib.ctm_log_norm_per_site(h, ctypes.byref(v)), h)
+    return v.value
+
+
+def ctm_init_env_random(h, seed):
+    _check(_lib.ctm_init_env_random(h, seed), h)
+
+
+def ctm_wait_probe(limit_cycles, arrive, flag, stream=None):
+    """Returns the status (CTM_OK or CTM_ERR_TIMEOUT); flag: a torch int32 CUDA tensor."""
+    st = _lib.ctm_wait_probe(int(limit_cycles), int(arrive), ctypes.c_void_p(flag.data_ptr()), _stream_ptr(stream))
+    if st not in (CTM_OK, CTM_ERR_TIMEOUT):
+        _check(st)
+    return st
 
 
 def ctm_run(h):
@@ -397,3 +419,9 @@ class CTMRG:
 
     def corner_spectra(self):
         return ctm_corner_spectra(self.h, self.chi)
+
+    def log_norm_per_site(self):
+        return ctm_log_norm_per_site(self.h)
+
+    def init_env_random(self, seed):
+        ctm_init_env_random(self.h, seed)

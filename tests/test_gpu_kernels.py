@@ -110,3 +110,40 @@ def test_svd_rank_deficient(ctm):
     assert np.max(np.abs(Sh[:5] - sref[:5]) / sref[:5]) < 1e-12
     assert np.max(Sh[5:]) < 1e-13 * Sh[0]
     assert np.max(np.abs((U.cpu().numpy() * Sh) @ V.cpu().numpy().T - G)) < 1e-13
+
+
+def test_svd_reports_converged(ctm):
+    """The first int of the SVD workspace is the Jacobi status: 0 when the
+    rotations settled within the sweep cap."""
+    k = 144
+    rng = np.random.default_rng(5)
+    G = rng.standard_normal((k, k)) * np.logspace(0, -12, k)[None, :]
+    U = torch.empty((k, k), dtype=torch.float64, device="cuda")
+    V = torch.empty((k, k), dtype=torch.float64, device="cuda")
+    S = torch.empty(k, dtype=torch.float64, device="cuda")
+    ws = torch.full((ctm.ctm_svd_workspace_bytes(k),), 0xFF, dtype=torch.uint8, device="cuda")
+    ctm.ctm_svd(dev(G), k, U, S, V, ws)
+    torch.cuda.synchronize()
+    assert int(ws[:4].view(torch.int32).item()) == 0
+
+
+def test_bounded_wait_gives_up_and_context_survives(ctm):
+    """Failure detection without a fault: a thread waits on an mbarrier that
+    nothing arrives on, with a short limit (1e6 cycles, ~0.5 ms).  The wait
+    must give up, the call report CTM_ERR_TIMEOUT, and the device keep
+    working: the same probe with an arrival succeeds and a GEMM runs."""
+    flag = torch.zeros(1, dtype=torch.int32, device="cuda")
+    assert ctm.ctm_wait_probe(1_000_000, 0, flag) == ctm.CTM_ERR_TIMEOUT
+    assert int(flag.item()) == 1
+    assert ctm.ctm_wait_probe(1_000_000, 1, flag) == ctm.CTM_OK
+    assert int(flag.item()) == 0
+    rng = np.random.default_rng(2)
+    A = rng.integers(-100, 100, size=(130, 70)).astype(np.float64)
+    B = rng.integers(-100, 100, size=(70, 50)).astype(np.float64)
+    C = torch.zeros((130, 50), dtype=torch.float64, device="cuda")
+    ws = torch.zeros(ctm.ctm_gemm_ozaki_workspace_bytes(130, 50, 70, 3), dtype=torch.uint8, device="cuda")
+    ctm.ctm_gemm_ozaki(0, 0, 130, 50, 70, 1.0, dev(A), 70, dev(B), 50, 0.0, C, 50, 3, ws)
+    torch.cuda.synchronize()
+    np.testing.assert_array_equal(C.cpu().numpy(), A @ B)
+    with pytest.raises(ctm.CtmError):
+        ctm.ctm_wait_probe(0, 0, flag)

@@ -100,3 +100,75 @@ def test_corner_apply_shape(ctm):
     torch.cuda.synchronize()
     err = (Y - ref).abs().max().item()
     assert err < 2.0 ** -30 * E.abs().max().item() * X.abs().max().item() * N
+
+
+# More tiles than the GB300's 152 SMs on the direct (non split-K) path: the
+# persistent grid then walks several tiles per CTA, carrying the stage ring
+# phases and the TMEM accumulator hand-off from one tile to the next.
+MULTI_TILE = [(64000, 64, 64), (64000, 144, 256), (64000, 192, 256), (40000, 144, 600)]
+
+
+def run_ld(ctm, A, B, tA, tB, slices, ldc, fill=7.0):
+    """Like run(), with the output written at row stride ldc > N; the
+    columns past N must keep their fill value."""
+    M = A.shape[1] if tA else A.shape[0]
+    K = A.shape[0] if tA else A.shape[1]
+    N = B.shape[0] if tB else B.shape[1]
+    dA = torch.from_numpy(np.ascontiguousarray(A)).cuda()
+    dB = torch.from_numpy(np.ascontiguousarray(B)).cuda()
+    dC = torch.full((M, ldc), fill, dtype=torch.float64, device="cuda")
+    ws = torch.zeros(ctm.ctm_gemm_ozaki_workspace_bytes(M, N, K, slices), dtype=torch.uint8, device="cuda")
+    ctm.ctm_gemm_ozaki(tA, tB, M, N, K, 1.0, dA, A.shape[1], dB, B.shape[1], 0.0, dC, ldc, slices, ws)
+    torch.cuda.synchronize()
+    assert int(ws[:4].view(torch.int32).item()) == 0, "a bounded device wait gave up"
+    return dC.cpu().numpy()
+
+
+@pytest.mark.parametrize("M,N,K", MULTI_TILE)
+@pytest.mark.parametrize("tA", [0, 1])
+def test_exact_multi_tile_persistent(ctm, M, N, K, tA):
+    """Integer operands using the leading digit only: bit-exact over
+    hundreds of tiles per launch (tiles = ceil(M/128) x N-tiles > 152)."""
+    rng = np.random.default_rng(M + N + K + tA)
+    A = rng.integers(-255, 256, size=(K, M) if tA else (M, K)).astype(np.float64)
+    B = rng.integers(-255, 256, size=(K, N)).astype(np.float64)
+    ref = (A.T if tA else A) @ B
+    got = run(ctm, A, B, tA, 0, slices=3)
+    np.testing.assert_array_equal(got, ref)
+
+
+def test_exact_multi_tile_two_digits(ctm):
+    """Two-digit B on the persistent multi-tile path: level-1 sums drained
+    from TMEM every 256-wide chunk, across tiles."""
+    M, N, K = 40000, 144, 600
+    rng = np.random.default_rng(9)
+    A = rng.integers(-255, 256, size=(M, K)).astype(np.float64)
+    B = rng.integers(-65535, 65536, size=(K, N)).astype(np.float64)
+    B[0, :] = 65535.0
+    got = run(ctm, A, B, 0, 0, slices=2)
+    np.testing.assert_array_equal(got, A @ B)
+
+
+def test_exact_multi_tile_strided_output(ctm):
+    """Output rows at stride ldc = N + 40: exact values in the first N
+    columns, the rest untouched."""
+    M, N, K, ldc = 64000, 144, 256, 184
+    rng = np.random.default_rng(11)
+    A = rng.integers(-255, 256, size=(M, K)).astype(np.float64)
+    B = rng.integers(-255, 256, size=(N, K)).astype(np.float64)
+    got = run_ld(ctm, A, B, 0, 1, 3, ldc)
+    np.testing.assert_array_equal(got[:, :N], A @ B.T)
+    assert np.all(got[:, N:] == 7.0)
+
+
+@pytest.mark.parametrize("M,N,K", [(64000, 144, 256), (40000, 192, 600)])
+def test_random_multi_tile_within_slicing_bound(ctm, M, N, K):
+    """General FP64 data, 5 slices, multi-tile persistent path: every entry
+    within 2^(2-8s) max|row| max|col| K of the FP64 product."""
+    rng = np.random.default_rng(M + K)
+    A = rng.standard_normal((M, K)) * np.logspace(0, -6, M)[:, None]
+    B = rng.standard_normal((K, N)) * np.logspace(0, -6, N)[None, :]
+    ref = A @ B
+    got = run(ctm, A, B, 0, 0, 5)
+    bound = 2.0 ** (2 - 8 * 5) * np.abs(A).max(axis=1)[:, None] * np.abs(B).max(axis=0)[None, :] * K
+    assert np.all(np.abs(got - ref) <= bound)
