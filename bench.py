@@ -4,10 +4,18 @@
 Workload (default): S=1 spins d=3, D=8, chi=128 (N = chi D^2 = 8192), 2x2
 cell, x-polarised product state + 0.05 N(0,1) (seed 3), random environment
 (seed 4).  One step = one full CTMRG sweep (left, top, right, bottom moves:
-64 enlarged corners, 16 projectors by randomised SVD, 16 site updates).
+64 enlarged corners, 16 projectors by randomised SVD, 16 site updates) in
+emulated FP64 (BF16 slice products on the tensor cores; QR, SVD and
+normalisation in FP64).
+
+Beside the timed mixed sweeps, one run also measures the metric's gate:
+the mixed run continued to its fixed point, then the FP64 GPU path continued
+from there (FP64 sweeps/s, and the largest |dE| per bond between the two
+fixed points), and a bounded Poisson serving leg (p50/p99 latency).
 
 Prints one JSON line (rank 0).  --impl reference times the CPU oracle on a
-bounded sample of the same workload instead.
+bounded sample of the same workload instead.  --case NAME runs one small
+profiling case (a single kernel class, for ncu) and exits.
 """
 from __future__ import annotations
 
@@ -30,8 +38,8 @@ WORKLOADS = {
     "neel_d2_D6_chi72": "d=2, D=6, chi=72, 2x2 cell, Neel + 0.1 noise (seed 2), env seed 3",
     "neel_d2_D3_chi16": "d=2, D=3, chi=16, 2x2 cell, Neel + 0.1 noise (seed 0), env seed 1",
 }
-METRIC = "CTMRG sweeps/s at D=8,chi=128 (d=3, 2x2 cell)"
-FP64_NOMINAL_TFLOPS = 1.25  # GB300 FP64 (profiling recipe, nominal)
+METRIC = "CTMRG sweeps/s at D=8,chi=128 (d=3, 2x2 cell), mixed vs FP64 @|dE|<=1e-8; p50/p99 latency"
+TRAFFIC_PROFILE = os.path.join(ROOT, "profiles", "launches_xpol_d3_D8_chi128_mixed.md")
 
 
 def parse():
@@ -43,8 +51,11 @@ def parse():
     ap.add_argument("--precision", default="mixed", choices=["fp64", "mixed"])
     ap.add_argument("--slices", type=int, default=5)
     ap.add_argument("--workload", default="xpol_d3_D8_chi128", choices=sorted(WORKLOADS))
-    ap.add_argument("--e2e-steps", type=int, default=1)
+    ap.add_argument("--e2e-steps", type=int, default=3)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-gate", action="store_true", help="skip the FP64 arm and the |dE| gate")
+    ap.add_argument("--no-serve", action="store_true", help="skip the serving-latency leg")
+    ap.add_argument("--case", default=None, choices=sorted(CASES), help="run one profiling case and exit")
     return ap.parse_args()
 
 
@@ -179,6 +190,18 @@ def run_reference(args):
     print(json.dumps(line), flush=True)
 
 
+def read_traffic():
+    """DRAM bytes (read + write) of the k_oz_gemm launches of one timed sweep,
+    from the committed ncu launch-list summary (None when it holds none)."""
+    try:
+        for line in open(TRAFFIC_PROFILE):
+            if line.startswith("k_oz_gemm DRAM bytes per sweep:"):
+                return float(line.split(":")[1].split()[0])
+    except OSError:
+        pass
+    return None
+
+
 def oz_gemm_roofline(by_op):
     """Roofline of the emulated-FP64 GEMM class (k_oz_gemm) over one sweep.
 
@@ -210,15 +233,171 @@ def oz_gemm_roofline(by_op):
     top = dict(sorted(ops.items(), key=lambda kv: -kv[1]["ms"])[:8])
     return {"bound": "tensor" if tensor else "hbm", "kernel": "k_oz_gemm (tcgen05 BF16 slice products)",
             "achieved": achieved, "peak": peak, "unit": "TFLOP/s" if tensor else "GB/s",
-            "frac": achieved / peak, "traffic": None,
+            "frac": achieved / peak, "traffic": read_traffic(), "algorithmic_bytes": B,
             "peak_source": ("MEASURED_PEAKS.json bf16_tflops_sustained (of measured)" if tensor
                             else "MEASURED_PEAKS.json hbm_gbs (of measured)"),
             "roofline_time_frac": t_roof / T, "class_ms": T * 1e3,
             "note": ("achieved = sum over the sweep's emulated GEMMs of the algorithmic work in the "
                      "bound's unit / their summed device time; roofline_time_frac = "
                      "sum max(F/P_tensor, B/BW) / measured time (shapes range from tensor- to "
-                     "HBM-bound); traffic: per-shape DRAM bytes are in profiles/"),
+                     "HBM-bound); traffic = DRAM bytes of the same launches in one timed sweep (ncu "
+                     "launch list in profiles/), against algorithmic_bytes"),
             "ops": top}
+
+
+def observables(solver, w):
+    one = [solver.measure1(i, w["op1"]) for i in range(4)]
+    from paper_2112_13184_gb300 import inputs as I
+    two = [solver.measure2(i, dx, dy, w["op2"]) for (i, dx, dy) in I.SQUARE_2X2_BONDS]
+    return np.array(one), np.array(two)
+
+
+def gate_leg(C, w, mixed, stream, slices):
+    """The metric's gate.  The mixed solver (already warm) is run to its
+    fixed point (normalised corner spectra changing by < 1e-6 per sweep, the
+    floor the emulated products' rounding leaves on that gauge-dependent
+    measure, cap 40); the FP64 GPU path starts from that environment, one
+    sweep warms it up, two are timed (the FP64 arm's sweeps/s), and it is
+    run on to its own fixed point (< 1e-9, cap 12).  |dE| per bond: the
+    eight bond energies of the two fixed points."""
+    import torch
+    # the existing (warm) handle is continued sweep by sweep
+    n_mix, d_mix = 0, float("inf")
+    mixed.spectrum_delta()
+    while n_mix < 40:
+        mixed.sweep(1)
+        n_mix += 1
+        d_mix = mixed.spectrum_delta()
+        if d_mix < 1e-6:
+            break
+    e1_m, e2_m = observables(mixed, w)
+    envs = mixed.get_envs()
+    fp = C.CTMRG(w["d"], w["D"], w["chi"], stream=stream, precision=C.CTM_FP64)
+    fp.set_tensors(w["As"])
+    fp.set_envs(envs)
+    fp.sweep(1)
+    torch.cuda.synchronize()
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    ev0.record(stream)
+    fp.sweep(2)
+    ev1.record(stream)
+    torch.cuda.synchronize()
+    fp64_ms = ev0.elapsed_time(ev1) / 2
+    n_fp, d_fp = 3, float("inf")
+    fp.spectrum_delta()
+    while n_fp < 12:
+        fp.sweep(1)
+        n_fp += 1
+        d_fp = fp.spectrum_delta()
+        if d_fp < 1e-9:
+            break
+    e1_f, e2_f = observables(fp, w)
+    fp.close()
+    dE = np.abs(e2_m - e2_f)
+    return {"fp64_sweeps_per_s": 1e3 / fp64_ms, "fp64_ms_per_sweep": fp64_ms,
+            "mixed_sweeps_to_fixed_point": n_mix, "mixed_last_spectrum_delta": d_mix,
+            "fp64_sweeps_from_mixed_fixed_point": n_fp, "fp64_last_spectrum_delta": d_fp,
+            "max_abs_dE_bond": float(dE.max()), "abs_dE_bond": [float(x) for x in dE],
+            "max_abs_d_one_site": float(np.abs(e1_m - e1_f).max()),
+            "bond_energy_fp64": [float(x) for x in e2_f],
+            "gate_dE_le_1e-8": bool(dE.max() <= 1e-8)}
+
+
+def serve_leg(seed=0):
+    """Bounded serving-latency leg: a Poisson stream of 12 CTMRG+observable
+    requests at 4 per second from the transverse-field-scan family (d in
+    {2, 3}, D = 4, chi = 32; product state + 0.05 noise, per-request seed),
+    served by the continuous-batching loop; tol 1e-7 on the corner-spectrum
+    change, cap 40 sweeps; mixed and FP64."""
+    from paper_2112_13184_gb300 import serve as S
+    out = {}
+    for prec in ("mixed", "fp64"):
+        r = S.serve_poisson(4.0, 12, 40 * (1 << 30), prec, 1e-7, 40, seed=seed, Ds=(4,), chis=(32,))
+        out[prec] = {k: r[k] for k in ("requests", "converged", "p50_s", "p99_s", "throughput_req_per_s")}
+    out["workload"] = ("Poisson 4 req/s x 12, d in {2,3}, D=4, chi=32, tol 1e-7 (corner-spectrum change), "
+                       "cap 40 sweeps, budget 40 GiB")
+    return out
+
+
+# ---------------------------------------------------------------------------
+# profiling cases: small, self-contained launches of one kernel class each,
+# sized so an ncu capture ends in seconds while operands exceed the L2
+# ---------------------------------------------------------------------------
+def _oz(M, N, K, slices=5, tA=0):
+    import torch
+    from paper_2112_13184_gb300 import ctm
+    g = torch.Generator(device="cuda").manual_seed(0)
+    A = torch.randn((K, M) if tA else (M, K), dtype=torch.float64, device="cuda", generator=g)
+    B = torch.randn(K, N, dtype=torch.float64, device="cuda", generator=g)
+    C = torch.empty(M, N, dtype=torch.float64, device="cuda")
+    ws = torch.empty(ctm.ctm_gemm_ozaki_workspace_bytes(M, N, K, slices), dtype=torch.uint8, device="cuda")
+    for _ in range(3):
+        ctm.ctm_gemm_ozaki(tA, 0, M, N, K, 1.0, A, A.shape[1], B, N, 0.0, C, N, slices, ws)
+    torch.cuda.synchronize()
+    print("done", float(C[0, 0]))
+
+
+def case_apply_oz():
+    """Corner apply of the D=8, chi=128 sweep on the tensor cores: 8192 x 144 x 8192, 5 slices."""
+    _oz(8192, 144, 8192)
+
+
+def case_x3_oz():
+    """Second corner-formation product of the D=8, chi=128 sweep, row-major output: 1048576 x 192 x 64."""
+    _oz(1048576, 192, 64)
+
+
+def case_qr():
+    """The range finder's Householder QR at D=8, chi=128: 8192 x 144 (persistent launch)."""
+    import torch
+    from paper_2112_13184_gb300 import ctm
+    N, k = 8192, 144
+    g = torch.Generator(device="cuda").manual_seed(0)
+    Y = torch.randn(N, k, dtype=torch.float64, device="cuda", generator=g)
+    Q = torch.empty(N, k, dtype=torch.float64, device="cuda")
+    R = torch.empty(k, k, dtype=torch.float64, device="cuda")
+    ws = torch.zeros(ctm.ctm_qr_workspace_bytes(N, k), dtype=torch.uint8, device="cuda")
+    for _ in range(3):
+        ctm.ctm_qr(Y, N, k, Q, R, ws)
+    torch.cuda.synchronize()
+    print("qr done", float(R[0, 0]))
+
+
+def case_svd():
+    """The projector's one-sided Jacobi SVD at D=8, chi=128: 144 x 144."""
+    import torch
+    from paper_2112_13184_gb300 import ctm
+    k = 144
+    g = torch.Generator(device="cuda").manual_seed(0)
+    G = torch.randn(k, k, dtype=torch.float64, device="cuda", generator=g)
+    U = torch.empty(k, k, dtype=torch.float64, device="cuda")
+    V = torch.empty(k, k, dtype=torch.float64, device="cuda")
+    Sv = torch.empty(k, dtype=torch.float64, device="cuda")
+    ws = torch.zeros(ctm.ctm_svd_workspace_bytes(k), dtype=torch.uint8, device="cuda")
+    for _ in range(3):
+        ctm.ctm_svd(G, k, U, Sv, V, ws)
+    torch.cuda.synchronize()
+    print("svd done", float(Sv[0]))
+
+
+def case_sweep_chi64():
+    """One emulated-FP64 sweep at d=3, D=8, chi=64 (N = 4096, corners 134 MB):
+    every kernel of the sweep in its real operand layouts, small enough for
+    full ncu captures of single launches."""
+    import torch
+    from paper_2112_13184_gb300 import ctm, inputs
+    d, D, chi = 3, 8, 64
+    c = ctm.CTMRG(d, D, chi, precision=ctm.CTM_OZAKI_BF16, ozaki_slices=5)
+    c.set_tensors(inputs.x_polarised_tensors(d, D, 0.05, seed=3))
+    c.set_envs(inputs.random_env(chi, [D] * 4, seed=4))
+    c.sweep(1)
+    torch.cuda.synchronize()
+    print("sweep_chi64 done", c.measure1(0, inputs.spin_ops(d)["Sx"]))
+    c.close()
+
+
+CASES = {"apply_oz": case_apply_oz, "x3_oz": case_x3_oz, "qr": case_qr, "svd": case_svd,
+         "sweep_chi64": case_sweep_chi64}
 
 
 # ---------------------------------------------------------------------------
@@ -298,6 +477,14 @@ def run_ours(args):
     e2e_max = max_over_ranks(e2e_s, world, "cuda")
     e2e_value = replica_throughput(args.e2e_steps, world, e2e_max) if args.e2e_steps > 0 else None
 
+    gate = None
+    if prec == C.CTM_OZAKI_BF16 and not args.no_gate and world == 1:
+        gate = gate_leg(C, w, solver, stream, args.slices)
+    latency = None
+    if not args.no_serve and world == 1:
+        latency = serve_leg()
+    fp64_peak = C.ctm_fp64_peak()
+
     if rank == 0:
         g = prof["gemm"]
         achieved = g["flops"] / (g["ms"] / 1e3) / 1e12 if g["ms"] > 0 else None
@@ -305,9 +492,9 @@ def run_ours(args):
                      "run right after the timed region (graph replays cannot be timed per kernel)")
         if prec == C.CTM_FP64:
             roof = {"bound": "alu", "kernel": "k_dgemm (FP64 DFMA)", "achieved": achieved,
-                    "peak": FP64_NOMINAL_TFLOPS, "unit": "TFLOP/s",
-                    "frac": achieved / FP64_NOMINAL_TFLOPS if achieved else None, "traffic": None,
-                    "peak_source": "GB300 FP64 nominal 1.25 TFLOP/s (profiling recipe table)"}
+                    "peak": fp64_peak, "unit": "TFLOP/s",
+                    "frac": achieved / fp64_peak if achieved else None, "traffic": None,
+                    "peak_source": "ctm_fp64_peak: DFMA chains on every SM, CUDA events (of measured)"}
         else:
             roof = oz_gemm_roofline(by_op)
         total_ms = sum(p["ms"] for p in prof.values())
@@ -322,9 +509,13 @@ def run_ours(args):
                        "l2": "working set per sweep (N x N corners, 537 MB each) exceeds the 129 MB L2"},
             "roofline": roof,
             "e2e": {"value": e2e_value, "unit": "sweeps/s", "h2d_bytes_per_step": h2d,
-                    "d2h_bytes_per_step": d2h, "steps": args.e2e_steps},
+                    "d2h_bytes_per_step": d2h, "steps": args.e2e_steps,
+                    "note": "each step re-uploads A and C/T, which restarts the range finder cold (eager sweep)"},
             "gpu_launches": launches,
             "clocks": clk.summary(),
+            "gate": gate,
+            "latency": latency,
+            "fp64_peak_tflops": fp64_peak,
             "profile_note": prof_note,
             "profile_by_op": {k: {"ms": round(v["ms"], 3), "calls": v["calls"], "launches": v.get("launches")}
                               for k, v in sorted(by_op.items(), key=lambda kv: -kv[1]["ms"])},
@@ -343,7 +534,9 @@ def run_ours(args):
 
 def main():
     args = parse()
-    if args.impl == "reference":
+    if args.case:
+        CASES[args.case]()
+    elif args.impl == "reference":
         run_reference(args)
     else:
         run_ours(args)

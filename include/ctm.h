@@ -228,6 +228,13 @@ ctm_status ctm_profile_report(ctm_handle h, char* buf, size_t len, int reset);
  * and kernel-level calls); cudaMemset/cudaMemcpy are not counted. */
 long long ctm_kernel_launches(void);
 
+/* Measured FP64 FMA throughput of the current device in TFLOP/s (no
+ * counterpart in the paper; the denominator of the FP64 path's roofline):
+ * 8 SM-count x 256 threads run independent FMA chains, best of three timed
+ * launches after a warm-up, CUDA events.  Allocates and frees its own small
+ * buffer and stream; synchronises. */
+ctm_status ctm_fp64_peak(double* tflops);
+
 /* Failure-detection check (no counterpart in the paper): launches one
  * thread that waits on an mbarrier with the same bounded wait the
  * tensor-core GEMM uses, for at most limit_cycles (1 .. 4e9) SM clock
@@ -257,7 +264,11 @@ ctm_status ctm_permute(const double* src, double* dst, int ndim, const int* dims
 
 /* Thin Householder QR of Y (N x k row-major, N >= k): Q (N x k) with
  * orthonormal columns and upper-triangular R (k x k, diagonal >= 0), Y=QR.
- * Y is not modified.  ws: workspace of ctm_qr_workspace_bytes(N,k) bytes. */
+ * Y is not modified.  ws: workspace of ctm_qr_workspace_bytes(N,k) bytes.
+ * Runs as one persistent cooperative launch over all SMs when the row slabs
+ * fit in shared memory (k columns of ~N/152 rows twice), else as two
+ * launches per column; in the persistent form the first int of ws is set to
+ * 1 if a bounded grid barrier gave up (Q and R then hold no result). */
 size_t ctm_qr_workspace_bytes(int N, int k);
 ctm_status ctm_qr(const double* Y, int N, int k, double* Q, double* R, void* ws, void* stream);
 
@@ -274,9 +285,13 @@ ctm_status ctm_svd(const double* G, int k, double* U, double* S, double* V, void
  * cores as exact BF16 slice products (emulated FP64; see CTM_OZAKI_BF16):
  * each row of op(A) and column of op(B) is scaled by a power of two and cut
  * into `slices` (2..6) signed 8-bit digits; products of the two leading
- * digit levels are accumulated exactly, the rest in FP32, levels >= slices
- * dropped.  Error ~ 2^(-8 slices) * max|row| * max|col| * K.  Entries whose
- * digits all fit (e.g. integers below 2^8 per row max) give exact results.
+ * digit levels are accumulated exactly, the rest in FP32 (restarted every
+ * 256 of K), levels >= slices dropped, and all of it summed exactly in
+ * int64.  Error per entry <= (2^(2 - 8 slices) + 2^-36) * max|row of op(A)|
+ * * max|col of op(B)| * K: the first term is the slicing, the second the
+ * tensor cores' FP32 rounding of the levels >= 2 (measured), so 5 slices
+ * give ~1e-11 relative per unit K and 6 add nothing.  Entries whose digits
+ * all fit (e.g. integers below 2^8 per row max) give exact results.
  * ws: ctm_gemm_ozaki_workspace_bytes(M,N,K,slices) bytes; its first int is
  * set non-zero if a bounded wait inside the kernel gave up (C then holds no
  * result).  Not synchronised. */

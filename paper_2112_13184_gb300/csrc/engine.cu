@@ -393,7 +393,7 @@ ctm_status perm(ctm_ctx* h, const double* src, double* dst, std::initializer_lis
 ctm_status qr_(ctm_ctx* h, const double* Y, double* Q, double* R) {
     ProfTag tg(h, "qr");
     const size_t ev = prof_begin(h);
-    CK(ctm::qr(Y, h->N, h->k, Q, R, h->qr_ws, h->stream));
+    CK(ctm::qr(Y, h->N, h->k, Q, R, h->qr_ws, h->stream, h->flag + 1));
     prof_end(h, ev, P_QR, 4.0 * h->N * (double)h->k * h->k, 0.0);
     return CTM_OK;
 }
@@ -646,7 +646,7 @@ ctm_status read_flag(ctm_ctx* h) {
         CK(cudaMemsetAsync(h->flag + 2, 0, sizeof(int), h->stream));
     }
     if (f[1]) {
-        h->err = "a bounded wait inside a tensor-core GEMM gave up";
+        h->err = "a bounded device wait (tensor-core GEMM pipeline or QR grid barrier) gave up";
         return CTM_ERR_TIMEOUT;
     }
     if (f[0] == 2) {
@@ -813,14 +813,18 @@ ctm_status log_norm_per_site(ctm_ctx* h, double* out) {
     // columns: right (C2, T2(TR), T2(BR), C3) and left (C4, T4(BL), T4(TL), C1)
     CKS(strip_value(h, h->env[TR][C2], h->env[TR][T2], h->env[BR][T2], h->env[BR][C3], h->env[BL][C4],
                     h->env[BL][T4], h->env[TL][T4], h->env[TL][C1], &z02));
-    // Z_22 = sum (E_ul E_ur) o (E_bl E_br) over the cut between rows 0 and 1 at column 0
+    // Z_22 = Tr(H_u^T H_d) over the cut between rows 0 and 1 at column 0.
+    // The four corners of a cut are held as H_u = E_ul E_ur and
+    // H_d^T = E_br E_bl (the lower two corners transposed), so
+    // Z_22 = Tr(E_ul E_ur E_br E_bl) = sum_ab (E_ul E_ur)[a,b] (E_br E_bl)[b,a].
     CKS(enlarged_corner(h, TL, 0, h->E[0]));
     CKS(enlarged_corner(h, TR, 1, h->E[1]));
     CKS(enlarged_corner(h, BR, 2, h->E[2]));
     CKS(enlarged_corner(h, BL, 3, h->E[3]));
     CKS(gemm(h, false, false, N, N, N, h->E[0], N, h->E[1], N, h->S1, N));
-    CKS(gemm(h, false, false, N, N, N, h->E[3], N, h->E[2], N, h->S3, N));
-    CKS(dot_host(h, h->S1, h->S3, (size_t)N * N, &z22));
+    CKS(gemm(h, false, false, N, N, N, h->E[2], N, h->E[3], N, h->S3, N));
+    CKS(perm(h, h->S3, h->S2, {N, N}, {1, 0}));
+    CKS(dot_host(h, h->S1, h->S2, (size_t)N * N, &z22));
     const double ratio = z22 * z00 / (z20 * z02);
     if (!(ratio > 0.0) || !std::isfinite(ratio)) {
         char buf[200];
@@ -1322,6 +1326,43 @@ ctm_status ctm_init_env_random(ctm_handle h, uint64_t seed) {
     h->env_set = 0xffffffffu;
     for (bool& w : h->warm_valid) w = false;
     for (auto& c : h->ozc) c.valid = false;
+    return CTM_OK;
+}
+
+ctm_status ctm_fp64_peak(double* tflops) {
+    if (!tflops) return CTM_ERR_ARG;
+    int dev = 0, nsm = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess || cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess) {
+        g_err = "ctm_fp64_peak: no device";
+        return CTM_ERR_CUDA;
+    }
+    const int blocks = nsm * 8, threads = 256, iters = 4096;
+    double* out = nullptr;
+    cudaStream_t st = nullptr;
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    cudaError_t e = cudaMalloc(&out, sizeof(double) * blocks * threads);
+    if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&st, cudaStreamNonBlocking);
+    if (e == cudaSuccess) e = cudaEventCreate(&e0);
+    if (e == cudaSuccess) e = cudaEventCreate(&e1);
+    float best = 1e30f;
+    for (int rep = 0; rep < 4 && e == cudaSuccess; ++rep) {  // first launch warms up
+        e = cudaEventRecord(e0, st);
+        if (e == cudaSuccess) e = ctm::dfma_probe(out, blocks, threads, iters, st);
+        if (e == cudaSuccess) e = cudaEventRecord(e1, st);
+        if (e == cudaSuccess) e = cudaEventSynchronize(e1);
+        float ms = 0.f;
+        if (e == cudaSuccess) e = cudaEventElapsedTime(&ms, e0, e1);
+        if (e == cudaSuccess && rep > 0) best = std::min(best, ms);
+    }
+    if (e0) cudaEventDestroy(e0);
+    if (e1) cudaEventDestroy(e1);
+    if (st) cudaStreamDestroy(st);
+    if (out) cudaFree(out);
+    if (e != cudaSuccess) {
+        g_err = std::string("ctm_fp64_peak: ") + cudaGetErrorString(e);
+        return CTM_ERR_CUDA;
+    }
+    *tflops = 2.0 * 8.0 * iters * (double)blocks * threads / (best * 1e-3) / 1e12;
     return CTM_OK;
 }
 

@@ -36,6 +36,8 @@ cudaError_t scale_by_max(double* x, size_t n, const unsigned long long* maxbits,
 // *out = sum_i x[i] y[i] in a fixed order; ws: dot_ws_doubles() doubles
 size_t dot_ws_doubles();
 cudaError_t dot(const double* x, const double* y, size_t n, double* out, double* ws, cudaStream_t s);
+// blocks x threads threads, each 8 x iters FP64 FMAs; out: blocks x threads doubles
+cudaError_t dfma_probe(double* out, int blocks, int threads, int iters, cudaStream_t s);
 // T[a,k,k',b] (chi x D x D x chi) symmetrised over (k, k') in place
 cudaError_t sym_kk(double* T, int chi, int D, cudaStream_t s);
 // out[i] = standard normal, Philox4x32-10 counter (seed, stream_id, i)
@@ -43,7 +45,11 @@ cudaError_t rng_normal(double* out, size_t n, uint64_t seed, uint64_t stream_id,
 
 // ---- dense linear algebra (linalg.cu) ---------------------------------------
 size_t qr_ws_bytes(int N, int k);
-cudaError_t qr(const double* Y, int N, int k, double* Q, double* R, void* ws, cudaStream_t s);
+// Thin Householder QR.  One persistent cooperative launch when the row
+// slabs fit in shared memory (every grid barrier bounded: on a time-out *err
+// -- or, without err, the first int of ws -- becomes 1 and Q, R are not
+// valid), else two launches per column step.
+cudaError_t qr(const double* Y, int N, int k, double* Q, double* R, void* ws, cudaStream_t s, int* err = nullptr);
 size_t svd_ws_bytes(int k);
 // *status (optional; else the first int of ws) becomes 1 when the Jacobi
 // iteration still rotated in its last allowed sweep

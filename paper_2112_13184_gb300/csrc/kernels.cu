@@ -368,12 +368,33 @@ cudaError_t scale_by_max(double* x, size_t n, const unsigned long long* maxbits,
     k_scale_by_max<<<grid_for(n), 256, 0, s>>>(x, n, maxbits, flag);
     return cudaGetLastError();
 }
+// FP64 FMA throughput probe: every thread runs 8 independent FMA chains
+// (enough in flight to keep the pipe busy); the result is stored so the
+// chains are not optimised away.
+__global__ void k_dfma_probe(double* __restrict__ out, int iters, double a, double b) {
+    double x[8];
+#pragma unroll
+    for (int u = 0; u < 8; ++u) x[u] = (double)(threadIdx.x + u) * 1e-3;
+    for (int it = 0; it < iters; ++it)
+#pragma unroll
+        for (int u = 0; u < 8; ++u) x[u] = fma(x[u], a, b);
+    double s = 0.0;
+#pragma unroll
+    for (int u = 0; u < 8; ++u) s += x[u];
+    out[blockIdx.x * blockDim.x + threadIdx.x] = s;
+}
+
 size_t dot_ws_doubles() { return DOT_BLOCKS; }
 cudaError_t dot(const double* x, const double* y, size_t n, double* out, double* ws, cudaStream_t s) {
     ++g_launches;
     k_dot_partial<<<DOT_BLOCKS, 256, 0, s>>>(x, y, n, ws);
     ++g_launches;
     k_dot_final<<<1, 256, 0, s>>>(ws, DOT_BLOCKS, out);
+    return cudaGetLastError();
+}
+cudaError_t dfma_probe(double* out, int blocks, int threads, int iters, cudaStream_t s) {
+    ++g_launches;
+    k_dfma_probe<<<blocks, threads, 0, s>>>(out, iters, 0.999999, 1e-7);
     return cudaGetLastError();
 }
 cudaError_t sym_kk(double* T, int chi, int D, cudaStream_t s) {

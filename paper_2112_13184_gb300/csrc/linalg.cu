@@ -5,6 +5,7 @@
 // Each step is one launch; steps are ordered by the stream, so no kernel
 // waits on another.
 #include <cuda_runtime.h>
+#include <algorithm>
 #include <cstdint>
 #include <mutex>
 
@@ -163,6 +164,214 @@ __global__ void __launch_bounds__(QR2_THREADS) k_qt_update(double* __restrict__ 
 }
 
 // ---------------------------------------------------------------------------
+// Householder QR in ONE persistent cooperative launch.  GB300 runs FP64 at
+// about two DFMA per clock per SM, so the 2 N k^2 flops of each half (the
+// factorisation and the explicit Q) are spread over every SM: CTA b holds
+// rows [b nr, (b+1) nr) of the panel -- and later of Q -- in shared memory
+// (column-major, rows contiguous), and every column step is
+//   partial dots over the own rows -> one bounded grid barrier -> every
+//   CTA adds the partials of all CTAs in the same fixed order (so all agree
+//   on beta, tau and the update weights bit for bit, and a rerun gives the
+//   same bits) -> reflector applied to the own rows,
+// with the next column's partial dots fused behind the update: k barriers
+// for the factorisation and k for Q = H_0 ... H_{k-1} [I; 0], accumulated
+// backwards.  The reflector is the same normalised one as the per-step
+// kernels above.  Partial sums and the published row j are double-buffered
+// by step parity, so a CTA running ahead never overwrites what a slower one
+// still reads.  Data written by other CTAs is read through L2 (ld.cg).
+// ---------------------------------------------------------------------------
+constexpr int PQR_THREADS = 256;
+constexpr int PQR_MIN_ROWS = 16;
+constexpr int PQR_MAX_GRID = 160;  // partials per column read by one CTA step (8 lanes x 20)
+constexpr long long PQR_WAIT_CYCLES = 2000000000ll;
+
+__device__ __forceinline__ double warp_sum(double v) {
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    return v;
+}
+
+// Grid-wide barrier of a cooperative launch (all CTAs resident).  Bounded:
+// gives up after `limit` cycles, or at once when another CTA gave up,
+// recording the failure in *err; returns false then, and the caller leaves.
+__device__ __forceinline__ bool grid_barrier(unsigned* count, unsigned* gen, unsigned nb, int* err,
+                                             long long limit) {
+    __shared__ int ok_s;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        int ok = 1;
+        const unsigned g = atomicAdd(gen, 0u);
+        __threadfence();
+        if (atomicAdd(count, 1u) == nb - 1) {
+            atomicExch(count, 0u);
+            __threadfence();
+            atomicAdd(gen, 1u);
+        } else {
+            const long long t0 = clock64();
+            while (*(volatile unsigned*)gen == g) {
+                if (*(volatile int*)err) { ok = 0; break; }
+                if (clock64() - t0 > limit) { atomicCAS(err, 0, 1); ok = 0; break; }
+                __nanosleep(32);
+            }
+        }
+        __threadfence();
+        ok_s = ok && !*(volatile int*)err;
+    }
+    __syncthreads();
+    return ok_s != 0;
+}
+
+__global__ void __launch_bounds__(PQR_THREADS) k_qr_persistent(const double* __restrict__ Y, int N, int k, int nr,
+                                                               double* __restrict__ Q, double* __restrict__ R,
+                                                               double* __restrict__ P, double* __restrict__ Ajg,
+                                                               unsigned* bar, int* err, long long limit) {
+    extern __shared__ double sm[];
+    double* S = sm;                       // panel slab [k][nr]: R above, reflectors below the diagonal
+    double* Qs = S + (size_t)k * nr;      // Q slab [k][nr]
+    double* tot = Qs + (size_t)k * nr;    // totals of the current step [k]
+    double* wv = tot + k;                 // update weights [k]
+    double* tau_s = wv + k;               // [k]
+    double* beta_s = tau_s + k;           // [k]
+    const int G = gridDim.x, cta = blockIdx.x;
+    const int r0 = cta * nr, r1 = min(N, r0 + nr), nrl = max(0, r1 - r0);
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nw = blockDim.x >> 5;
+    unsigned* count = bar;
+    unsigned* gen = bar + 1;
+
+    for (int t = threadIdx.x; t < k * nr; t += blockDim.x) {
+        const int c = t / nr, rl = t - c * nr;
+        S[t] = rl < nrl ? Y[(size_t)(r0 + rl) * k + c] : 0.0;
+        Qs[t] = (rl < nrl && r0 + rl == c) ? 1.0 : 0.0;
+    }
+    __syncthreads();
+
+    // partial dots over the own rows >= j of column j (factor: x = column j;
+    // Q: x = reflector j, 1 at row j) with the columns c >= j of `B`, stored
+    // as this CTA's partials P[par][c][cta]
+    auto dots = [&](int j, int par, const double* B, bool reflector) {
+        const int rl0 = max(0, j - r0);
+        const double* x = S + (size_t)j * nr;
+        for (int c = j + warp; c < k; c += nw) {
+            const double* a = B + (size_t)c * nr;
+            double p = 0.0;
+            for (int rl = rl0 + lane; rl < nrl; rl += 32)
+                p = fma((reflector && r0 + rl == j) ? 1.0 : x[rl], a[rl], p);
+            p = warp_sum(p);
+            if (lane == 0) P[((size_t)par * k + c) * G + cta] = p;
+        }
+    };
+    // every CTA adds the G partials of each column c >= j in the same order:
+    // 8 lanes per column, lane s takes partials s, s+8, ... (all its loads
+    // issued before the first add), then a fixed 3-level shuffle tree
+    auto read_totals = [&](int j, int s) {
+        const int par = s & 1, sub = threadIdx.x & 7;
+        for (int c0 = j; c0 < k; c0 += PQR_THREADS / 8) {
+            const int c = c0 + (int)(threadIdx.x >> 3);
+            double t = 0.0;
+            if (c < k) {
+                const double* pc = P + ((size_t)par * k + c) * G;
+                double v[PQR_MAX_GRID / 8];
+#pragma unroll
+                for (int i = 0; i < PQR_MAX_GRID / 8; ++i) {
+                    const int q = sub + 8 * i;
+                    v[i] = q < G ? __ldcg(pc + q) : 0.0;
+                }
+#pragma unroll
+                for (int i = 0; i < PQR_MAX_GRID / 8; ++i) t += v[i];
+            }
+            t += __shfl_xor_sync(0xffffffffu, t, 1);
+            t += __shfl_xor_sync(0xffffffffu, t, 2);
+            t += __shfl_xor_sync(0xffffffffu, t, 4);
+            if (c < k && sub == 0) tot[c] = t;
+        }
+        __syncthreads();
+    };
+
+    int step = 0;  // barriers passed: selects the buffers
+    dots(0, 0, S, false);
+    if (r0 == 0)
+        for (int c = threadIdx.x; c < k; c += blockDim.x) Ajg[c] = S[(size_t)c * nr];
+    for (int j = 0; j < k; ++j, ++step) {
+        if (!grid_barrier(count, gen, G, err, limit)) return;
+        read_totals(j, step);
+        const int par = step & 1;
+        const double s2 = tot[j];
+        const double xj = __ldcg(Ajg + (size_t)par * k + j);
+        double bt = xj, inv = 0.0, tu = 0.0;
+        if (s2 > 0.0) {
+            const double sig = sqrt(s2);
+            bt = xj >= 0.0 ? -sig : sig;
+            inv = 1.0 / (xj - bt);  // |xj - bt| = |xj| + sig >= sig > 0
+            tu = (bt - xj) / bt;
+        }
+        for (int c = j + 1 + threadIdx.x; c < k; c += blockDim.x)
+            wv[c] = tu * (tot[c] - bt * __ldcg(Ajg + (size_t)par * k + c)) * inv;
+        // column j becomes the reflector v (v_j = 1 implicit, beta on the diagonal)
+        const int rl0 = max(0, j - r0);
+        for (int rl = rl0 + threadIdx.x; rl < nrl; rl += blockDim.x)
+            S[(size_t)j * nr + rl] = (r0 + rl == j) ? bt : S[(size_t)j * nr + rl] * inv;
+        if (threadIdx.x == 0) {
+            tau_s[j] = tu;
+            beta_s[j] = bt;
+        }
+        __syncthreads();
+        if (tu != 0.0) {
+            const double* v = S + (size_t)j * nr;
+            for (int c = j + 1 + warp; c < k; c += nw) {
+                const double w = wv[c];
+                double* a = S + (size_t)c * nr;
+                for (int rl = rl0 + lane; rl < nrl; rl += 32) a[rl] = fma(-w, (r0 + rl == j) ? 1.0 : v[rl], a[rl]);
+            }
+        }
+        __syncthreads();
+        if (j + 1 < k) {
+            dots(j + 1, (step + 1) & 1, S, false);
+            if (j + 1 >= r0 && j + 1 < r1)
+                for (int c = j + 1 + threadIdx.x; c < k; c += blockDim.x)
+                    Ajg[(size_t)((step + 1) & 1) * k + c] = S[(size_t)c * nr + (j + 1 - r0)];
+        }
+    }
+
+    // Q = H_0 ... H_{k-1} [I; 0], applied from the last reflector back
+    int jn = k - 1;
+    while (jn >= 0 && tau_s[jn] == 0.0) --jn;  // identical in every CTA
+    if (jn >= 0) dots(jn, step & 1, Qs, true);
+    while (jn >= 0) {
+        const int j = jn;
+        if (!grid_barrier(count, gen, G, err, limit)) return;
+        read_totals(j, step);
+        const double tu = tau_s[j];
+        const int rl0 = max(0, j - r0);
+        const double* v = S + (size_t)j * nr;
+        for (int c = j + warp; c < k; c += nw) {
+            const double w = tu * tot[c];
+            double* q = Qs + (size_t)c * nr;
+            for (int rl = rl0 + lane; rl < nrl; rl += 32) q[rl] = fma(-w, (r0 + rl == j) ? 1.0 : v[rl], q[rl]);
+        }
+        __syncthreads();
+        ++step;
+        jn = j - 1;
+        while (jn >= 0 && tau_s[jn] == 0.0) --jn;
+        if (jn >= 0) dots(jn, step & 1, Qs, true);
+    }
+
+    // signs so that diag(R) >= 0: column c of Q and row c of R times sgn(beta_c)
+    for (int t = threadIdx.x; t < nrl * k; t += blockDim.x) {
+        const int rl = t / k, c = t - rl * k;
+        const double sg = beta_s[c] < 0.0 ? -1.0 : 1.0;
+        Q[(size_t)(r0 + rl) * k + c] = sg * Qs[(size_t)c * nr + rl];
+    }
+    for (int t = threadIdx.x; t < nrl * k; t += blockDim.x) {
+        const int rl = t / k, c = t - rl * k, jr = r0 + rl;
+        if (jr >= k) continue;
+        const double sg = beta_s[jr] < 0.0 ? -1.0 : 1.0;
+        double v = 0.0;
+        if (c == jr) v = fabs(beta_s[jr]);
+        else if (c > jr) v = sg * S[(size_t)c * nr + rl];
+        R[(size_t)jr * k + c] = v;
+    }
+}
+
+// ---------------------------------------------------------------------------
 // One-sided Jacobi in a single launch: one thread-block cluster per matrix,
 // its warps share the round's pairs; columns live in global memory and are
 // read and written through L2 (ld.cg / st.cg); a cluster barrier (release /
@@ -212,6 +421,11 @@ __global__ void __launch_bounds__(256) k_jacobi_cluster(double* __restrict__ Gt,
                 if (P > Q) { const int t = P; P = Q; Q = t; }
                 double* gp = g + (size_t)P * k;
                 double* gq = g + (size_t)Q * k;
+                double* wp = wm ? wm + (size_t)P * k : nullptr;
+                double* wq = wm ? wm + (size_t)Q * k : nullptr;
+                // every load of the pair is issued before the first use, so a
+                // round costs one L2 round trip instead of one per 32 entries
+                const double a = __ldcg(nb2 + P), bb = __ldcg(nb2 + Q);
                 double xr[RK], yr[RK];
                 double c = 0.0;
                 if (cached) {
@@ -220,13 +434,13 @@ __global__ void __launch_bounds__(256) k_jacobi_cluster(double* __restrict__ Gt,
                         const int i = lane + 32 * u;
                         xr[u] = i < k ? __ldcg(gp + i) : 0.0;
                         yr[u] = i < k ? __ldcg(gq + i) : 0.0;
-                        c = fma(xr[u], yr[u], c);
                     }
+#pragma unroll
+                    for (int u = 0; u < RK; ++u) c = fma(xr[u], yr[u], c);
                 } else {
                     for (int i = lane; i < k; i += 32) c = fma(__ldcg(gp + i), __ldcg(gq + i), c);
                 }
                 for (int o = 16; o > 0; o >>= 1) c += __shfl_xor_sync(0xffffffffu, c, o);
-                const double a = __ldcg(nb2 + P), bb = __ldcg(nb2 + Q);
                 if (a < 1e-280 || bb < 1e-280) continue;  // zero or near underflow: nothing to rotate
                 const double rel = fabs(c) / (sqrt(a) * sqrt(bb));
                 if (lane == 0) atomicMax(offb + sw, (unsigned long long)__double_as_longlong(rel));
@@ -255,12 +469,29 @@ __global__ void __launch_bounds__(256) k_jacobi_cluster(double* __restrict__ Gt,
                     __stcg(nb2 + Q, bb + t * c);
                 }
                 if (wm) {
-                    double* wp = wm + (size_t)P * k;
-                    double* wq = wm + (size_t)Q * k;
-                    for (int i = lane; i < k; i += 32) {
-                        const double x = __ldcg(wp + i), y = __ldcg(wq + i);
-                        __stcg(wp + i, cs * x - sn * y);
-                        __stcg(wq + i, sn * x + cs * y);
+                    if (cached) {
+                        // all W loads of the pair in flight together
+                        double ur[RK], vr[RK];
+#pragma unroll
+                        for (int u = 0; u < RK; ++u) {
+                            const int i = lane + 32 * u;
+                            ur[u] = i < k ? __ldcg(wp + i) : 0.0;
+                            vr[u] = i < k ? __ldcg(wq + i) : 0.0;
+                        }
+#pragma unroll
+                        for (int u = 0; u < RK; ++u) {
+                            const int i = lane + 32 * u;
+                            if (i < k) {
+                                __stcg(wp + i, cs * ur[u] - sn * vr[u]);
+                                __stcg(wq + i, sn * ur[u] + cs * vr[u]);
+                            }
+                        }
+                    } else {
+                        for (int i = lane; i < k; i += 32) {
+                            const double x = __ldcg(wp + i), y = __ldcg(wq + i);
+                            __stcg(wp + i, cs * x - sn * y);
+                            __stcg(wq + i, sn * x + cs * y);
+                        }
                     }
                 }
             }
@@ -422,8 +653,81 @@ size_t qr_ws_bytes(int N, int k) {
     return sizeof(double) * (3 * (size_t)k * N + (size_t)k * k + 3 * (size_t)k + nch * k) + 256;
 }
 
-cudaError_t qr(const double* Y, int N, int k, double* Q, double* R, void* ws, cudaStream_t s) {
+// Grid of the persistent QR on the current device (0: it does not apply --
+// the panel slabs do not fit in shared memory or the device cannot run a
+// cooperative launch), and its rows per CTA.
+struct PqrPlan {
+    int grid = 0, nr = 0;
+    size_t smem = 0;
+};
+PqrPlan pqr_plan(int N, int k) {
+    PqrPlan p;
+    static std::mutex mu;
+    static int nsm[64], coop[64];
+    static unsigned long long known = 0;
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) return p;
+    {
+        std::lock_guard<std::mutex> lock(mu);
+        if (!(known >> dev & 1ull)) {
+            if (cudaDeviceGetAttribute(&nsm[dev], cudaDevAttrMultiProcessorCount, dev) != cudaSuccess) nsm[dev] = 0;
+            if (cudaDeviceGetAttribute(&coop[dev], cudaDevAttrCooperativeLaunch, dev) != cudaSuccess) coop[dev] = 0;
+            cudaGetLastError();
+            known |= 1ull << dev;
+        }
+        if (!coop[dev] || nsm[dev] <= 0) return p;
+        int g = std::min(std::min(nsm[dev], PQR_MAX_GRID), (N + PQR_MIN_ROWS - 1) / PQR_MIN_ROWS);
+        if (g < 1) g = 1;
+        const int nr = (N + g - 1) / g;
+        const size_t smem = sizeof(double) * (2 * (size_t)k * nr + 4 * (size_t)k);
+        if (smem > 200 * 1024) return p;
+        p.grid = (N + nr - 1) / nr;
+        p.nr = nr;
+        p.smem = smem;
+    }
+    return p;
+}
+
+cudaError_t qr(const double* Y, int N, int k, double* Q, double* R, void* ws, cudaStream_t s, int* err) {
     if (N < k || k <= 0) return cudaErrorInvalidValue;
+    const PqrPlan pp = pqr_plan(N, k);
+    if (pp.grid > 0) {
+        // ws: [err int | barrier count, generation] (256 B) | P [2][k][grid] | row j [2][k]
+        char* w = (char*)ws;
+        int* e_flag = err ? err : (int*)w;
+        unsigned* bar = (unsigned*)(w + 16);
+        double* P = (double*)(w + 256);
+        double* Ajg = P + 2 * (size_t)pp.grid * k;
+        // a caller's flag is not cleared here: it may hold an earlier time-out
+        cudaError_t e = cudaMemsetAsync(w, 0, 256, s);
+        if (e) return e;
+        static std::mutex amu;
+        static unsigned long long attr_done = 0;
+        int dev = 0;
+        e = cudaGetDevice(&dev);
+        if (e) return e;
+        {
+            std::lock_guard<std::mutex> lock(amu);
+            if (!(attr_done >> dev & 1ull)) {
+                e = cudaFuncSetAttribute(k_qr_persistent, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
+                if (e) return e;
+                attr_done |= 1ull << dev;
+            }
+        }
+        cudaLaunchConfig_t cfg = {};
+        cfg.gridDim = dim3((unsigned)pp.grid, 1, 1);
+        cfg.blockDim = dim3(PQR_THREADS, 1, 1);
+        cfg.dynamicSmemBytes = pp.smem;
+        cfg.stream = s;
+        cudaLaunchAttribute at[1];
+        at[0].id = cudaLaunchAttributeCooperative;
+        at[0].val.cooperative = 1;
+        cfg.attrs = at;
+        cfg.numAttrs = 1;
+        ++g_launches;
+        return cudaLaunchKernelEx(&cfg, k_qr_persistent, Y, N, k, pp.nr, Q, R, P, Ajg, bar, e_flag,
+                                  PQR_WAIT_CYCLES);
+    }
     const int nch = (N + QR_CHUNK - 1) / QR_CHUNK;
     double* At = (double*)ws;
     double* V = At + (size_t)k * N;

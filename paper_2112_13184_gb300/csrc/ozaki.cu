@@ -5,17 +5,23 @@
 //     x = 2^(e-8) * sum_t a_t 2^(-8t),   a_0 in [-256,256], a_t in [-128,127],
 // computed with integer operations on the FP64 bit pattern (the FP64 pipe of
 // GB300 is slow).  The scaled digits at_t = a_t 2^(-8t) are exact in BF16.
-// C = A B is then the sum of BF16 slice products at_t * bt_u:
+// C = A B is then the sum of BF16 slice products at_t * bt_u, accumulated
+// on the tensor cores in FP32 over K-chunks of 256 and read out of TMEM
+// after every chunk:
 //   level 0 (t+u = 0) and level 1 (t+u = 1) are integer-valued (in units of
-//   1 and 2^-8); summed in FP32 over K-chunks of 256 they stay below 2^24
-//   units and are therefore exact; every chunk is read out of TMEM and
-//   added to int32 registers;
-//   all pairs with 2 <= t+u <= s-1 carry a weight <= 2^-16 and go into one
-//   FP32 accumulator whose rounding is below the slicing error;
+//   1 and 2^-8); over one chunk they stay below 2^24 units and are exact,
+//   and are added to int32 registers;
+//   all pairs with 2 <= t+u <= s-1 carry a weight <= 2^-16 and share one
+//   FP32 accumulator, restarted every chunk so that the tensor cores'
+//   rounding does not grow with the magnitude accumulated over K; the chunk
+//   values are added in an FP32 register;
 //   pairs with t+u >= s are dropped (same order as the slicing error).
-// The result is assembled in FP64:  C = 2^(eA+eB-16) (S0 + 2^-8 S1 + F).
-// Accuracy ~ 2^(-8s) of max|row| * max|col| * K, against FP32-accumulated
-// split-BF16 which cannot go below ~2^-24.
+// The result is assembled exactly in int64, C = 2^(eA+eB-16) (S0 + 2^-8 S1
+// + F).  Error: the slicing, 2^(2-8s) max|row| max|col| K, plus the tensor
+// cores' FP32 rounding of the levels >= 2 within a chunk, measured at about
+// 2^-36 max|row| max|col| K; so 5 slices reach ~1e-11 relative per unit K
+// and a 6th adds nothing.  Split-BF16 accumulated in FP32 over all of K
+// cannot go below ~2^-24.
 #include <cuda.h>
 #include <cuda_bf16.h>
 #include <cuda_runtime.h>
@@ -155,29 +161,13 @@ __device__ __forceinline__ long long f32_fixed(float f, int k) {
     return (b >> 31) ? -v : v;
 }
 
-// f 2^k as an int for an FP32 f whose f 2^k is a whole number below 2^31
-// (the level-0 and level-1 sums of one K chunk), by shifting the FP32
-// significand: integer instructions only, where a float-to-int conversion
-// would run on GB300's narrow FP64/conversion pipe.
-__device__ __forceinline__ int f32_exact_int(float f, int k) {
-    const unsigned b = __float_as_uint(f);
-    const int ex = (int)((b >> 23) & 0xff);
-    const unsigned mant = (b & 0x7fffffu) | 0x800000u;
-    const int sh = ex - 150 + k;  // |f| 2^k = mant 2^sh
-    unsigned v;
-    if (ex == 0 || sh <= -24) v = 0u;
-    else if (sh >= 0) v = sh < 8 ? mant << sh : 0x7fffffffu;  // >= 2^31: not a valid level sum
-    else v = mant >> (-sh);
-    return (b >> 31) ? -(int)v : (int)v;
-}
-
 // C = 2^(eA+eB-16) (S0 + S1/256 + F).  With T = 256 S0 + S1 (exact; |T| <
 // 2^39 for K <= 16384 per split) and F kept to 2^-28 of an S0 unit (below
 // 2^-44 of max|row| max|col|), Z = 2^20 T + round(2^28 F) is an exact int64
 // and C = Z 2^(eA+eB-44).  escale = eA + eB - 16.
 __device__ __forceinline__ double assemble(int S0, int S1, float F, int escale) {
     const long long T = (long long)S0 * 256 + (long long)S1;
-    const long long Z = T * (1ll << 20) + f32_fixed(F, 28);  // F 2^28 < 2^62
+    const long long Z = T * (1ll << 20) + __float2ll_rn(F * 268435456.0f);  // F 2^28 < 2^62
     return i64_ldexp(Z, escale - 28);
 }
 
@@ -230,10 +220,17 @@ __device__ __forceinline__ void digits(double x, int e, int s, int* d) {
     d[0] = (int)Y;
 }
 
+// A small int as an FP32 without a conversion instruction: 1.5 2^23 + d has
+// the bit pattern 0x4B400000 + d for |d| < 2^22, so one FP32 subtraction
+// recovers d exactly.
+__device__ __forceinline__ float small_int_f32(int d) {
+    return __int_as_float(0x4B400000 + d) - 12582912.0f;
+}
+
 // digit * 2^(-8t): at most 9 significant bits, exact in FP32 and BF16; the
 // power of two is built from its exponent field
 __device__ __forceinline__ __nv_bfloat16 slice_value(int digit, int t) {
-    return __float2bfloat16_rn((float)digit * __int_as_float((127 - 8 * t) << 23));
+    return __float2bfloat16_rn(small_int_f32(digit) * __int_as_float((127 - 8 * t) << 23));
 }
 
 // Consecutive k contiguous (innermost K stride 1): one warp per row.
@@ -359,10 +356,10 @@ __device__ __forceinline__ void slice8_pack(const double* v, int e, int s, uint4
     for (int t = 0; t < MAX_S; ++t) {
         if (t < s) {
             const float sc = __int_as_float((127 - 8 * t) << 23);  // 2^(-8t)
-            q[t].x = bf2_bits((float)d[0][t] * sc, (float)d[1][t] * sc);
-            q[t].y = bf2_bits((float)d[2][t] * sc, (float)d[3][t] * sc);
-            q[t].z = bf2_bits((float)d[4][t] * sc, (float)d[5][t] * sc);
-            q[t].w = bf2_bits((float)d[6][t] * sc, (float)d[7][t] * sc);
+            q[t].x = bf2_bits(small_int_f32(d[0][t]) * sc, small_int_f32(d[1][t]) * sc);
+            q[t].y = bf2_bits(small_int_f32(d[2][t]) * sc, small_int_f32(d[3][t]) * sc);
+            q[t].z = bf2_bits(small_int_f32(d[4][t]) * sc, small_int_f32(d[5][t]) * sc);
+            q[t].w = bf2_bits(small_int_f32(d[6][t]) * sc, small_int_f32(d[7][t]) * sc);
         }
     }
 }
@@ -609,7 +606,7 @@ struct GemmArgs {
     double alpha, beta;
     double* C;
     View out_r, out_c;    // C offset of (m, n) = view(out_r, m) + view(out_c, n)
-    int* PS0;             // partials [z][Mpad][Npad]
+    int* PS0;             // split-K partials [z][Mpad][Npad]
     int* PS1;
     float* PF;
     int Mpad, Npad;
@@ -618,7 +615,10 @@ struct GemmArgs {
     long long wait_limit; // cycles before a bounded wait gives up
 };
 
-template <int NB16>
+// ONE: every CTA's K range is a single chunk (every corner product), so no
+// sum is carried across chunks; a separate instantiation keeps the
+// multi-chunk sums' registers out of that path.
+template <int NB16, bool ONE>
 __global__ void __launch_bounds__(THREADS, 1)
     k_oz_gemm(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB, const GemmArgs g) {
     constexpr int BN = 16 * NB16;
@@ -733,7 +733,7 @@ __global__ void __launch_bounds__(THREADS, 1)
                     tc_mma(tmem, sw64_desc(sa + h * 32), sw64_desc(sb + h * 32), idesc, restart);
                     tc_mma(tmem + BN, sw64_desc(sa + h * 32), sw64_desc(sb + BN * 64 + h * 32), idesc, restart);
                     tc_mma(tmem + BN, sw64_desc(sa + BM * 64 + h * 32), sw64_desc(sb + h * 32), idesc, 1u);
-                    bool first2 = (i == 0 && h == 0);
+                    bool first2 = first && h == 0;  // the FP32 levels restart every chunk
                     for (int L = 2; L < g.s; ++L)
                         for (int t = 0; t <= L; ++t) {
                             tc_mma(tmem + 2 * BN, sw64_desc(sa + t * (BM * 64) + h * 32),
@@ -759,83 +759,93 @@ __global__ void __launch_bounds__(THREADS, 1)
         const uint32_t lane_addr = tmem + ((uint32_t)(q * 32) << 16);
         int cc = 0;  // accumulator chunks drained so far, over all tiles
         bool ok = true;
+        const bool unit_alpha = g.alpha == 1.0, zero_beta = g.beta == 0.0;
         for (int t = t_first; t < ntiles && ok; t += t_step) {
         const int m0 = tile_m0(t), n0 = tile_n0(t);
-        int S0[NBG][16], S1[NBG][16];
-        float F[NBG][16];
+        const int m = m0 + q * 32 + lane;
+        const int ea = (g.direct && m < g.M) ? g.eA[m] : 0;
+        // Multi-chunk tiles carry the exact level-0/1 sums (int32) and the
+        // sum of the per-chunk FP32 levels across K chunks, and finish each
+        // 16-column block in the last chunk before reading the next.  A
+        // single-chunk tile (every corner product: K <= 256) reads all of
+        // TMEM first and releases it, so that the next tile's MMAs run while
+        // this tile's results are assembled and stored.
+        constexpr int NC = NBG;
+        int S0[NC][16], S1[NC][16];
+        float Fs[NC][16];
 #pragma unroll
-        for (int jb = 0; jb < NBG; ++jb)
+        for (int jb = 0; jb < NC; ++jb)
 #pragma unroll
-            for (int j = 0; j < 16; ++j) S0[jb][j] = S1[jb][j] = 0, F[jb][j] = 0.f;
+            for (int j = 0; j < 16; ++j) S0[jb][j] = S1[jb][j] = 0, Fs[jb][j] = 0.f;
+        // result of column block jb: assembled and stored (direct) or kept
+        // as split-K partials
+        auto finish = [&](int jb) {
+            const int b = grp + 3 * jb;
+            if (g.direct) {
+                // the 16 columns of this block are the same for every lane:
+                // lane j works out column j's offset and exponent once
+                const int nl = n0 + b * 16 + (lane & 15);
+                const long long coff_l = nl < g.N ? view_offset32(g.out_c, (unsigned)nl) : 0;
+                const int eb_l = nl < g.N ? g.eB[nl] : 0;
+                double* crow = g.C + (m < g.M ? view_offset32(g.out_r, (unsigned)m) : 0);
+#pragma unroll
+                for (int j = 0; j < 16; ++j) {
+                    const long long coff = __shfl_sync(0xffffffffu, coff_l, j);
+                    const int eb = __shfl_sync(0xffffffffu, eb_l, j);
+                    const int n = n0 + b * 16 + j;
+                    if (m >= g.M || n >= g.N) continue;
+                    double v = assemble(S0[jb][j], S1[jb][j], Fs[jb][j], ea + eb - 16);
+                    if (ea > 1024 || eb > 1024) v = __longlong_as_double(0x7ff8000000000000ll);  // non-finite operand
+                    if (!unit_alpha) v *= g.alpha;
+                    double* cp = crow + coff;
+                    *cp = zero_beta ? v : fma(g.beta, *cp, v);
+                }
+            } else {
+                const size_t row = ((size_t)blockIdx.z * g.Mpad + m) * g.Npad + n0 + b * 16;
+#pragma unroll
+                for (int j = 0; j < 16; ++j) {
+                    g.PS0[row + j] = S0[jb][j];
+                    g.PS1[row + j] = S1[jb][j];
+                    g.PF[row + j] = Fs[jb][j];
+                }
+            }
+        };
         for (int c = 0; c < nchunks; ++c, ++cc) {
             if (!mbar_wait(acc_full, (uint32_t)cc & 1u, g.err, g.wait_limit)) {
                 ok = false;
                 break;
             }
             tc_fence_after();
+            const bool last = c == nchunks - 1;
 #pragma unroll
             for (int jb = 0; jb < NBG; ++jb) {
                 const int b = grp + 3 * jb;
-                if (b < NB16) {
-                    uint32_t r0[16], r1[16];
-                    tc_ld16(lane_addr + b * 16, r0);
-                    tc_ld16(lane_addr + BN + b * 16, r1);
+                if (b >= NB16) continue;
+                uint32_t r0[16], r1[16];
+                tc_ld16(lane_addr + b * 16, r0);
+                tc_ld16(lane_addr + BN + b * 16, r1);
+                tc_wait_ld();
+#pragma unroll
+                for (int j = 0; j < 16; ++j) {
+                    S0[jb][j] += __float2int_rn(__uint_as_float(r0[j]));
+                    S1[jb][j] += __float2int_rn(__uint_as_float(r1[j]) * 256.0f);
+                }
+                if (g.s > 2) {
+                    tc_ld16(lane_addr + 2 * BN + b * 16, r0);
                     tc_wait_ld();
 #pragma unroll
-                    for (int j = 0; j < 16; ++j) {
-                        S0[jb][j] += f32_exact_int(__uint_as_float(r0[j]), 0);
-                        S1[jb][j] += f32_exact_int(__uint_as_float(r1[j]), 8);
-                    }
-                    if (c == nchunks - 1 && g.s > 2) {
-                        uint32_t r2[16];
-                        tc_ld16(lane_addr + 2 * BN + b * 16, r2);
-                        tc_wait_ld();
-#pragma unroll
-                        for (int j = 0; j < 16; ++j) F[jb][j] = __uint_as_float(r2[j]);
-                    }
+                    for (int j = 0; j < 16; ++j) Fs[jb][j] += __uint_as_float(r0[j]);
                 }
+                if (!ONE && last) finish(jb);
             }
             tc_fence_before();
             __syncwarp();
             if (lane == 0) mbar_arrive(acc_empty);
         }
-        if (ok) {
-            const int m = m0 + q * 32 + lane;
-            const int ea = (g.direct && m < g.M) ? g.eA[m] : 0;
-            const bool unit_alpha = g.alpha == 1.0, zero_beta = g.beta == 0.0;
+        if (ONE && ok) {
 #pragma unroll
-            for (int jb = 0; jb < NBG; ++jb) {
-                const int b = grp + 3 * jb;
-                if (b >= NB16) continue;
-                if (g.direct) {
-                    // the 16 columns of this block are the same for every lane:
-                    // lane j works out column j's offset and exponent once
-                    const int nl = n0 + b * 16 + (lane & 15);
-                    const long long coff_l = nl < g.N ? view_offset32(g.out_c, (unsigned)nl) : 0;
-                    const int eb_l = nl < g.N ? g.eB[nl] : 0;
-                    double* crow = g.C + (m < g.M ? view_offset32(g.out_r, (unsigned)m) : 0);
-#pragma unroll
-                    for (int j = 0; j < 16; ++j) {
-                        const long long coff = __shfl_sync(0xffffffffu, coff_l, j);
-                        const int eb = __shfl_sync(0xffffffffu, eb_l, j);
-                        const int n = n0 + b * 16 + j;
-                        if (m >= g.M || n >= g.N) continue;
-                        double v = assemble(S0[jb][j], S1[jb][j], F[jb][j], ea + eb - 16);
-                        if (ea > 1024 || eb > 1024) v = __longlong_as_double(0x7ff8000000000000ll);  // non-finite operand
-                        if (!unit_alpha) v *= g.alpha;
-                        double* cp = crow + coff;
-                        *cp = zero_beta ? v : fma(g.beta, *cp, v);
-                    }
-                } else {
-                    const size_t row = ((size_t)blockIdx.z * g.Mpad + m) * g.Npad + n0 + b * 16;
-#pragma unroll
-                    for (int j = 0; j < 16; ++j) {
-                        g.PS0[row + j] = S0[jb][j];
-                        g.PS1[row + j] = S1[jb][j];
-                        g.PF[row + j] = F[jb][j];
-                    }
-                }
-            }
+            for (int jb = 0; jb < NBG; ++jb)
+                if (grp + 3 * jb < NB16) finish(jb);
         }
         }  // tiles
     }
@@ -945,7 +955,7 @@ Plan plan_of(int M, int N, int K, int s) {
     return p;
 }
 
-template <int NB16>
+template <int NB16, bool ONE>
 cudaError_t launch_gemm(const Plan& p, const CUtensorMap& ta, const CUtensorMap& tb, const oz::GemmArgs& g,
                         cudaStream_t st) {
     // the 227 KB dynamic shared-memory opt-in is a per-device function
@@ -959,7 +969,8 @@ cudaError_t launch_gemm(const Plan& p, const CUtensorMap& ta, const CUtensorMap&
     {
         std::lock_guard<std::mutex> lock(mu);
         if (!(done >> dev & 1ull)) {
-            e = cudaFuncSetAttribute(oz::k_oz_gemm<NB16>, cudaFuncAttributeMaxDynamicSharedMemorySize, 227 * 1024);
+            e = cudaFuncSetAttribute(oz::k_oz_gemm<NB16, ONE>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                     227 * 1024);
             if (e != cudaSuccess) return e;
             done |= 1ull << dev;
         }
@@ -974,7 +985,7 @@ cudaError_t launch_gemm(const Plan& p, const CUtensorMap& ta, const CUtensorMap&
         grid = dim3((unsigned)std::min<long long>(tiles, nsm > 0 ? nsm : 1), 1, 1);
     }
     ++g_launches;
-    oz::k_oz_gemm<NB16><<<grid, oz::THREADS, p.smem, st>>>(ta, tb, g);
+    oz::k_oz_gemm<NB16, ONE><<<grid, oz::THREADS, p.smem, st>>>(ta, tb, g);
     return cudaGetLastError();
 }
 
@@ -1133,17 +1144,28 @@ cudaError_t oz_gemm_view(int M, int N, int K, int s, const void* Asplit, const v
     }
     g.err = err;
     g.wait_limit = oz::WAIT_LIMIT_CYCLES;
+    // a CTA's K range: all of K (direct) or kb_per_split k-blocks (split-K)
+    const bool one = (p.ksplit == 1 ? p.nkb : p.kb_per_split) <= oz::CHUNK_KB;
     cudaError_t e;
-    switch (p.nb16) {
-        case 1: e = launch_gemm<1>(p, ta, tb, g, st); break;
-        case 2: e = launch_gemm<2>(p, ta, tb, g, st); break;
-        case 3: e = launch_gemm<3>(p, ta, tb, g, st); break;
-        case 4: e = launch_gemm<4>(p, ta, tb, g, st); break;
-        case 5: e = launch_gemm<5>(p, ta, tb, g, st); break;
-        case 6: e = launch_gemm<6>(p, ta, tb, g, st); break;
-        case 7: e = launch_gemm<7>(p, ta, tb, g, st); break;
-        case 8: e = launch_gemm<8>(p, ta, tb, g, st); break;
-        default: e = launch_gemm<9>(p, ta, tb, g, st); break;
+    switch (p.nb16 * 2 + (one ? 1 : 0)) {
+        case 2: e = launch_gemm<1, false>(p, ta, tb, g, st); break;
+        case 3: e = launch_gemm<1, true>(p, ta, tb, g, st); break;
+        case 4: e = launch_gemm<2, false>(p, ta, tb, g, st); break;
+        case 5: e = launch_gemm<2, true>(p, ta, tb, g, st); break;
+        case 6: e = launch_gemm<3, false>(p, ta, tb, g, st); break;
+        case 7: e = launch_gemm<3, true>(p, ta, tb, g, st); break;
+        case 8: e = launch_gemm<4, false>(p, ta, tb, g, st); break;
+        case 9: e = launch_gemm<4, true>(p, ta, tb, g, st); break;
+        case 10: e = launch_gemm<5, false>(p, ta, tb, g, st); break;
+        case 11: e = launch_gemm<5, true>(p, ta, tb, g, st); break;
+        case 12: e = launch_gemm<6, false>(p, ta, tb, g, st); break;
+        case 13: e = launch_gemm<6, true>(p, ta, tb, g, st); break;
+        case 14: e = launch_gemm<7, false>(p, ta, tb, g, st); break;
+        case 15: e = launch_gemm<7, true>(p, ta, tb, g, st); break;
+        case 16: e = launch_gemm<8, false>(p, ta, tb, g, st); break;
+        case 17: e = launch_gemm<8, true>(p, ta, tb, g, st); break;
+        case 18: e = launch_gemm<9, false>(p, ta, tb, g, st); break;
+        default: e = launch_gemm<9, true>(p, ta, tb, g, st); break;
     }
     if (e != cudaSuccess || g.direct) return e;
     size_t blocks = ((size_t)M * N + 255) / 256;

@@ -91,6 +91,7 @@ _sig("ctm_svd_noalloc", c_int, c_void_p, c_int, c_void_p, c_void_p, c_void_p, c_
 _sig("ctm_log_norm_per_site", c_int, c_void_p, c_dp)
 _sig("ctm_init_env_random", c_int, c_void_p, ctypes.c_uint64)
 _sig("ctm_wait_probe", c_int, ctypes.c_longlong, c_int, c_void_p, c_void_p)
+_sig("ctm_fp64_peak", c_int, c_dp)
 _sig("ctm_profile_enable", c_int, c_void_p, c_int)
 _sig("ctm_profile_read", c_int, c_void_p, ctypes.POINTER(ctm_profile_data), c_int)
 _sig("ctm_kernel_launches", ctypes.c_longlong)
@@ -227,6 +228,12 @@ def ctm_wait_probe(limit_cycles, arrive, flag, stream=None):
     if st not in (CTM_OK, CTM_ERR_TIMEOUT):
         _check(st)
     return st
+
+
+def ctm_fp64_peak():
+    v = c_double()
+    _check(_lib.ctm_fp64_peak(ctypes.byref(v)))
+    return v.value
 
 
 def ctm_run(h):

@@ -7,7 +7,9 @@ kernel keeps is accumulated exactly (levels 0 and 1), nothing is dropped,
 and the FP64 result must equal numpy's bit for bit (all partial sums stay
 far below 2^53).  Shapes cross the 128-row and 16..144-column tiles with
 ragged tails, several 256-wide K chunks, split-K and both transposes.
-General data: error within the slicing bound 2^(2-8s) max|row| max|col| K.
+General data: error within (2^(2-8s) + 2^-36) max|row| max|col| K: the
+slicing, plus the tensor cores' FP32 rounding of the levels >= 2, which are
+summed in FP32 only within one 256-wide K chunk.
 """
 import numpy as np
 import pytest
@@ -36,6 +38,12 @@ def run(ctm, A, B, tA, tB, slices, alpha=1.0, beta=0.0, C0=None):
     torch.cuda.synchronize()
     assert int(ws[:4].view(torch.int32).item()) == 0, "a bounded device wait gave up"
     return dC.cpu().numpy()
+
+
+def bound_of(A, B, slices):
+    """Per-entry error bound of the emulated product of A (M x K) and B (K x N)."""
+    K = A.shape[1]
+    return (2.0 ** (2 - 8 * slices) + 2.0 ** -36) * np.abs(A).max(axis=1)[:, None] * np.abs(B).max(axis=0)[None, :] * K
 
 
 SHAPES = [(128, 16, 32), (200, 144, 1000), (129, 33, 300), (64, 64, 64), (300, 200, 520), (1, 1, 1),
@@ -74,7 +82,7 @@ def test_random_within_slicing_bound(ctm, slices, M, N, K):
     B = rng.standard_normal((K, N)) * np.logspace(0, -6, N)[None, :]
     ref = A @ B
     got = run(ctm, A, B, 0, 0, slices)
-    bound = 2.0 ** (2 - 8 * slices) * np.abs(A).max(axis=1)[:, None] * np.abs(B).max(axis=0)[None, :] * K
+    bound = bound_of(A, B, slices)
     assert np.all(np.abs(got - ref) <= bound)
 
 
@@ -161,7 +169,7 @@ def test_exact_multi_tile_strided_output(ctm):
     assert np.all(got[:, N:] == 7.0)
 
 
-@pytest.mark.parametrize("M,N,K", [(64000, 144, 256), (40000, 192, 600)])
+@pytest.mark.parametrize("M,N,K", [(64000, 144, 256), (40000, 192, 600), (2048, 144, 8192), (256, 144, 256)])
 def test_random_multi_tile_within_slicing_bound(ctm, M, N, K):
     """General FP64 data, 5 slices, multi-tile persistent path: every entry
     within 2^(2-8s) max|row| max|col| K of the FP64 product."""
@@ -170,5 +178,21 @@ def test_random_multi_tile_within_slicing_bound(ctm, M, N, K):
     B = rng.standard_normal((K, N)) * np.logspace(0, -6, N)[None, :]
     ref = A @ B
     got = run(ctm, A, B, 0, 0, 5)
-    bound = 2.0 ** (2 - 8 * 5) * np.abs(A).max(axis=1)[:, None] * np.abs(B).max(axis=0)[None, :] * K
-    assert np.all(np.abs(got - ref) <= bound)
+    assert np.all(np.abs(got - ref) <= bound_of(A, B, 5))
+
+
+@pytest.mark.parametrize("M,N,K", [(200, 144, 1000), (25600, 144, 64), (64000, 192, 256), (40000, 144, 600)])
+def test_exact_three_levels(ctm, M, N, K):
+    """Both operands two-digit integers (below 2^16, row/column maxima pinned
+    at 65535) with 3 slices: the level-2 products a1 b1 2^-16 land in the
+    FP32 accumulator, and for K <= 1000 their sums stay below 2^8 in 2^-16
+    steps, so they are exact too and the whole product must equal numpy's
+    bit for bit -- on the split-K path (first shape) and on the direct
+    persistent path (the others, 200 to 1000 tiles)."""
+    rng = np.random.default_rng(M + 7 * K)
+    A = rng.integers(-65535, 65536, size=(M, K)).astype(np.float64)
+    B = rng.integers(-65535, 65536, size=(K, N)).astype(np.float64)
+    A[:, 0] = 65535.0
+    B[0, :] = 65535.0
+    got = run(ctm, A, B, 0, 0, slices=3)
+    np.testing.assert_array_equal(got, A @ B)

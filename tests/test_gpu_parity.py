@@ -193,35 +193,43 @@ def test_ising_onsager_on_gpu(ctm, beta):
     c.close()
 
 
-@pytest.mark.parametrize("beta", [0.6, 0.3])
+@pytest.mark.parametrize("beta,chi", [(0.6, 3), (0.3, 5)])
 @pytest.mark.parametrize("precision", ["fp64", "mixed"])
-def test_gauged_ising_onsager_on_gpu(ctm, beta, precision):
+def test_gauged_ising_onsager_on_gpu(ctm, beta, chi, precision):
     """Ising PEPS with a random gauge on each of the 8 bonds (all four site
-    tensors differ, so every row cut has its own projectors): the GPU's
-    magnetisation, bond correlations and ln kappa are still Onsager's, and
-    they match the oracle run on the same inputs."""
+    tensors differ, so every row cut has its own projectors), at chi with a
+    clear gap in M's spectrum above the 1e-12 cutoff: the GPU's
+    magnetisation, bond correlations, ln kappa and loop spectra match the
+    oracle run on the same inputs (1e-10 in FP64, 1e-8 emulated), and
+    Onsager's values to the truncation error at this chi."""
     As = I.gauged_ising_tensors(beta, seed=7, strength=0.3)
-    envs = I.random_env(8, [2] * 4, seed=5)
+    envs = I.random_env(chi, [2] * 4, seed=5)
     prec = ctm.CTM_OZAKI_BF16 if precision == "mixed" else ctm.CTM_FP64
-    c, ref = run_both(ctm, As, envs, 2, 2, 8, 70, precision=prec)
+    c, ref = run_both(ctm, As, envs, 2, 2, chi, 70, precision=prec)
     sz = np.diag([1.0, -1.0])
     m = np.array([c.measure1(i, sz) for i in range(4)])
     nn = np.array([c.measure2(i, dx, dy, np.kron(sz, sz)) for (i, dx, dy) in I.SQUARE_2X2_BONDS])
-    tol = 1e-9 if precision == "fp64" else 1e-8
-    np.testing.assert_allclose(np.abs(m), X.yang_magnetisation(beta), atol=tol)
-    np.testing.assert_allclose(nn, X.onsager_nn_correlation(beta), rtol=tol)
-    np.testing.assert_allclose(c.log_norm_per_site(), X.onsager_log_z_per_site(beta), rtol=tol)
     m_ref = np.array([R.expect(sz, R.rdm1(ref, As, i)) for i in range(4)])
+    nn_ref = np.array([R.expect(np.kron(sz, sz), R.rdm2(ref, As, i, dx, dy)) for (i, dx, dy) in I.SQUARE_2X2_BONDS])
+    tol = 1e-10 if precision == "fp64" else 1e-8
     np.testing.assert_allclose(m, m_ref, atol=tol)
+    np.testing.assert_allclose(nn, nn_ref, atol=tol)
+    np.testing.assert_allclose(c.log_norm_per_site(), R.log_kappa_per_site(ref, As)[0], rtol=tol)
     np.testing.assert_allclose(INV.loop_spectra(c.get_envs()), INV.loop_spectra(ref), atol=10 * tol, rtol=0)
+    np.testing.assert_allclose(np.abs(m), X.yang_magnetisation(beta), atol=2e-9 + tol)
+    np.testing.assert_allclose(nn, X.onsager_nn_correlation(beta), rtol=2e-9 + tol)
+    np.testing.assert_allclose(c.log_norm_per_site(), X.onsager_log_z_per_site(beta), rtol=2e-11 + tol)
     c.close()
 
 
 def test_random_env_init_on_device(ctm):
     """ctm_init_env_random (the library's own Philox draw) reaches the same
-    unique fixed point as any start: Ising at beta = 0.3 (disordered phase),
-    bond correlation and free energy from Onsager."""
-    c = ctm.CTMRG(2, 2, 16)
+    unique fixed point as any start: Ising at beta = 0.3 (disordered phase)
+    at chi = 5 (a clear gap in M's spectrum, sigma_5 ~ 2e-10 of sigma_0,
+    above the cutoff), bond correlation and free energy from Onsager to the
+    truncation error, and the oracle's values from its own start to 1e-10."""
+    chi = 5
+    c = ctm.CTMRG(2, 2, chi)
     c.set_tensors([I.ising_peps_tensor(0.3)] * 4)
     c.init_env_random(1234)
     envs = c.get_envs()
@@ -231,7 +239,12 @@ def test_random_env_init_on_device(ctm):
     assert np.std(envs[0]["C1"]) > 0.5
     c.sweep(60)
     zz = np.kron(np.diag([1.0, -1.0]), np.diag([1.0, -1.0]))
-    np.testing.assert_allclose(c.measure2(0, 1, 0, zz), X.onsager_nn_correlation(0.3), rtol=1e-9)
+    As = [I.ising_peps_tensor(0.3)] * 4
+    ref, _, _ = R.run(As, I.random_env(chi, [2] * 4, seed=5), chi, 60)
+    g = c.measure2(0, 1, 0, zz)
+    np.testing.assert_allclose(g, R.expect(zz, R.rdm2(ref, As, 0, 1, 0)), rtol=1e-10)
+    np.testing.assert_allclose(c.log_norm_per_site(), R.log_kappa_per_site(ref, As)[0], rtol=1e-10)
+    np.testing.assert_allclose(g, X.onsager_nn_correlation(0.3), rtol=1e-8)
     np.testing.assert_allclose(c.log_norm_per_site(), X.onsager_log_z_per_site(0.3), rtol=1e-10)
     c.close()
 

@@ -220,12 +220,19 @@ def test_bond_list_golden():
     assert tuple(rows) == I.SQUARE_2X2_BONDS
 
 
-@pytest.fixture(scope="module", params=[0.6, 0.3])
+# (beta, chi) with a clear gap in the spectrum of M at chi and sigma_chi well
+# above the 1e-12 cutoff (3e-8 and 1.8e-10 of sigma_0): larger chi reach
+# directions at the FP64 noise floor of M, where rounding decides which
+# directions survive the cutoff and the fixed point is not well posed.
+GAUGED_CASES = [(0.6, 3), (0.3, 5)]
+
+
+@pytest.fixture(scope="module", params=GAUGED_CASES)
 def gauged_ising(request):
-    beta = request.param
+    beta, chi = request.param
     As = I.gauged_ising_tensors(beta, seed=7, strength=0.3)
-    envs = I.random_env(8, [2] * 4, seed=5)
-    envs, n, delta = R.run(As, envs, 8, 70)
+    envs = I.random_env(chi, [2] * 4, seed=5)
+    envs, n, delta = R.run(As, envs, chi, 70)
     return beta, As, envs
 
 
@@ -249,9 +256,10 @@ def test_gauged_ising_onsager(gauged_ising):
     c = np.array([R.expect(np.kron(sz, sz), R.rdm2(envs, As, i, dx, dy)) for (i, dx, dy) in I.SQUARE_2X2_BONDS])
     lk, sign = R.log_kappa_per_site(envs, As)
     assert sign > 0
-    np.testing.assert_allclose(np.abs(m), X.yang_magnetisation(beta), atol=1e-9)
-    np.testing.assert_allclose(c, X.onsager_nn_correlation(beta), rtol=1e-9)
-    np.testing.assert_allclose(lk, X.onsager_log_z_per_site(beta), rtol=1e-10)
+    # truncation-limited at these chi (the error of the kept chi directions)
+    np.testing.assert_allclose(np.abs(m), X.yang_magnetisation(beta), atol=2e-9)
+    np.testing.assert_allclose(c, X.onsager_nn_correlation(beta), rtol=2e-9)
+    np.testing.assert_allclose(lk, X.onsager_log_z_per_site(beta), rtol=2e-11)
 
 
 def chi_bond_gauge(envs, chi, seed, strength=0.3):
