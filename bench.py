@@ -254,21 +254,20 @@ def observables(solver, w):
 
 def gate_leg(C, w, mixed, stream, slices):
     """The metric's gate.  The mixed solver (already warm) is run to its
-    fixed point (normalised corner spectra changing by < 1e-6 per sweep, the
-    floor the emulated products' rounding leaves on that gauge-dependent
-    measure, cap 40); the FP64 GPU path starts from that environment, one
-    sweep warms it up, two are timed (the FP64 arm's sweeps/s), and it is
-    run on to its own fixed point (< 1e-9, cap 12).  |dE| per bond: the
-    eight bond energies of the two fixed points."""
+    fixed point (gauge-invariant loop moments changing by < 1e-10 per sweep,
+    cap 40); the FP64 GPU path starts from that environment, one sweep warms
+    it up, two are timed (the FP64 arm's sweeps/s), and it is run on to its
+    own fixed point (< 1e-11, cap 12).  |dE| per bond: the eight bond
+    energies of the two fixed points."""
     import torch
     # the existing (warm) handle is continued sweep by sweep
     n_mix, d_mix = 0, float("inf")
-    mixed.spectrum_delta()
+    mixed.loop_delta()
     while n_mix < 40:
         mixed.sweep(1)
         n_mix += 1
-        d_mix = mixed.spectrum_delta()
-        if d_mix < 1e-6:
+        d_mix = mixed.loop_delta()
+        if d_mix < 1e-10:
             break
     e1_m, e2_m = observables(mixed, w)
     envs = mixed.get_envs()
@@ -284,19 +283,19 @@ def gate_leg(C, w, mixed, stream, slices):
     torch.cuda.synchronize()
     fp64_ms = ev0.elapsed_time(ev1) / 2
     n_fp, d_fp = 3, float("inf")
-    fp.spectrum_delta()
+    fp.loop_delta()
     while n_fp < 12:
         fp.sweep(1)
         n_fp += 1
-        d_fp = fp.spectrum_delta()
-        if d_fp < 1e-9:
+        d_fp = fp.loop_delta()
+        if d_fp < 1e-11:
             break
     e1_f, e2_f = observables(fp, w)
     fp.close()
     dE = np.abs(e2_m - e2_f)
     return {"fp64_sweeps_per_s": 1e3 / fp64_ms, "fp64_ms_per_sweep": fp64_ms,
-            "mixed_sweeps_to_fixed_point": n_mix, "mixed_last_spectrum_delta": d_mix,
-            "fp64_sweeps_from_mixed_fixed_point": n_fp, "fp64_last_spectrum_delta": d_fp,
+            "mixed_sweeps_to_fixed_point": n_mix, "mixed_last_loop_delta": d_mix,
+            "fp64_sweeps_from_mixed_fixed_point": n_fp, "fp64_last_loop_delta": d_fp,
             "max_abs_dE_bond": float(dE.max()), "abs_dE_bond": [float(x) for x in dE],
             "max_abs_d_one_site": float(np.abs(e1_m - e1_f).max()),
             "bond_energy_fp64": [float(x) for x in e2_f],
@@ -307,15 +306,15 @@ def serve_leg(seed=0):
     """Bounded serving-latency leg: a Poisson stream of 12 CTMRG+observable
     requests at 4 per second from the transverse-field-scan family (d in
     {2, 3}, D = 4, chi = 32; product state + 0.05 noise, per-request seed),
-    served by the continuous-batching loop; tol 1e-7 on the corner-spectrum
-    change, cap 40 sweeps; mixed and FP64."""
+    served by the continuous-batching loop; converged when the loop moments
+    change by < 1e-10 per sweep, cap 60 sweeps; mixed and FP64."""
     from paper_2112_13184_gb300 import serve as S
     out = {}
     for prec in ("mixed", "fp64"):
-        r = S.serve_poisson(4.0, 12, 40 * (1 << 30), prec, 1e-7, 40, seed=seed, Ds=(4,), chis=(32,))
+        r = S.serve_poisson(4.0, 12, 40 * (1 << 30), prec, 1e-10, 60, seed=seed, Ds=(4,), chis=(32,))
         out[prec] = {k: r[k] for k in ("requests", "converged", "p50_s", "p99_s", "throughput_req_per_s")}
-    out["workload"] = ("Poisson 4 req/s x 12, d in {2,3}, D=4, chi=32, tol 1e-7 (corner-spectrum change), "
-                       "cap 40 sweeps, budget 40 GiB")
+    out["workload"] = ("Poisson 4 req/s x 12, d in {2,3}, D=4, chi=32, converged at loop-moment change "
+                       "< 1e-10, cap 60 sweeps, budget 40 GiB")
     return out
 
 

@@ -89,11 +89,19 @@ typedef struct {
                                starts from that cut's basis of the previous sweep
                                (one subspace iteration per sweep, no extra power
                                iterations); reset by ctm_set_tensor / ctm_set_env */
+    int conv_measure;       /* ctm_run's convergence measure: 0 = the normalised
+                               corner spectra (ctm_spectrum_delta), 1 = the
+                               gauge-invariant loop moments (ctm_loop_delta)   */
+    int fp64_refine;        /* != 0 with CTM_OZAKI_BF16: once ctm_run's measure
+                               falls below 1e-8 (about where the emulated
+                               products' rounding holds it) the handle switches
+                               to FP64 contractions for the remaining sweeps and
+                               stays in FP64 afterwards                          */
 } ctm_options;
 
 /* Defaults: chi=16, max_sweeps=100, tol=1e-10, FP64, 5 slices,
  * p=max(8,chi/8) (when rsvd_oversample<=0), q=2, cutoff 1e-12, seed 0,
- * exact_svd_max_n=256, rsvd_warm_start=1. */
+ * exact_svd_max_n=256, rsvd_warm_start=1, conv_measure=0, fp64_refine=0. */
 ctm_status ctm_default_options(ctm_options* opt);
 
 /* Device bytes a handle of this shape allocates (workspace included): the
@@ -131,8 +139,9 @@ ctm_status ctm_init_env_random(ctm_handle h, uint64_t seed);
  * its Jacobi sweep cap during these sweeps. */
 ctm_status ctm_sweep(ctm_handle h, int n);
 
-/* Sweeps until the normalised corner spectra change by less than opt.tol
- * (max-abs over the 16 corners) or opt.max_sweeps is reached.  Either
+/* Sweeps until the convergence measure (opt.conv_measure: the normalised
+ * corner spectra, max-abs over the 16 corners, or the loop moments of
+ * ctm_loop_delta) changes by less than opt.tol or opt.max_sweeps is reached.  Either
  * output pointer may be NULL.  Returns CTM_NOT_CONVERGED at the cap.
  * With CTM_OZAKI_BF16 the spectrum change levels off where the emulated
  * products' rounding sits (about 1e-7 at d=3, D=8, chi=128 with 5 slices),
@@ -163,6 +172,24 @@ ctm_status ctm_batch_sweep(const ctm_handle* hs, int n, int sweeps);
  * of the normalised corner spectra since this handle's previous call
  * (+infinity on the first call).  Synchronises the handle. */
 ctm_status ctm_spectrum_delta(ctm_handle h, double* delta);
+
+/* Switches the handle's contractions to `precision` (CTM_FP64, or
+ * CTM_OZAKI_BF16 for a handle created with it) for the following sweeps; the
+ * environment and the range finder's warm bases are kept, the captured
+ * sweep graph is rebuilt.  Lets a caller finish an emulated-FP64 run in
+ * FP64 (what opt.fp64_refine does inside ctm_run).  Synchronises. */
+ctm_status ctm_set_precision(ctm_handle h, int precision);
+
+/* Gauge-invariant convergence measure (Sec. 2.2 iterates "until
+ * convergence"; the measure is this library's): for each 2x2 block the
+ * corner loop L = C1 C2 C3 C4 around it (the network Z_00) is a similar
+ * matrix under any change of basis on the chi bonds, so its normalised
+ * moments Tr(L^p) / Tr(L)^p, p = 2, 3, 4, do not move with the non-orthogonal
+ * gauge the projectors leave, while single-corner singular values do (they
+ * keep changing at ~1e-8 after the network has converged to 1e-12).  Returns
+ * the max-abs change since this handle's previous call (+infinity on the
+ * first).  FP64 products; synchronises the handle. */
+ctm_status ctm_loop_delta(ctm_handle h, double* delta);
 
 /* Normalised singular values (sum 1) of every corner: out[site][corner][chi]. */
 ctm_status ctm_corner_spectra(ctm_handle h, double* out_host);

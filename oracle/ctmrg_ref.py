@@ -42,11 +42,13 @@ import numpy as np
 
 ENV_NAMES = ("C1", "T1", "C2", "T2", "C3", "T3", "C4", "T4")
 
-# Multi-operand einsums are evaluated as a chain of pairwise contractions
-# with no cap on the size of the intermediates.  (numpy's default cap makes
-# it fold the last three operands of an enlarged corner into one unblocked
-# loop, which takes minutes at D = 8.)  This fixes only the order in which
-# the sum of each einsum is evaluated, not what it sums.
+# Einsums are evaluated as chains of pairwise (BLAS) contractions with no
+# cap on the size of the intermediates.  (numpy's default cap makes it fold
+# the last three operands of an enlarged corner into one unblocked loop,
+# which takes minutes at D = 8.)  The two 8-operand strips of ln kappa keep
+# numpy's capped search, which there avoids a D^6 chi^2-sized intermediate.
+# This fixes only the order in which each einsum's sum is evaluated, not
+# what it sums.
 PAIRWISE = ("greedy", 1 << 40)
 
 
@@ -60,7 +62,7 @@ def _site(x, y, Lx, Ly):
 def double_layer(A):
     """a[(l l'), (u u'), (r r'), (d d')] = sum_s A[s,l,u,r,d] A[s,l',u',r',d']."""
     d, D1, D2, D3, D4 = A.shape
-    a = np.einsum("slurd,sLURD->lLuUrRdD", A, A)
+    a = np.einsum("slurd,sLURD->lLuUrRdD", A, A, optimize=PAIRWISE)
     return a.reshape(D1 * D1, D2 * D2, D3 * D3, D4 * D4)
 
 
@@ -151,14 +153,14 @@ def projectors(Qul, Qur, Qbr, Qbl, chi, cutoff=1e-12):
 # --------------------------------------------------------------------------
 def absorb_C1(C1, T1, P_up):
     """C1'[c, b] = sum_a P_up[a, c] (C1 T1)[a=(C1.c_T4, T1.k, T1.k'), b=T1.c_C2]."""
-    CT = np.einsum("gh,huUb->guUb", C1, T1)
+    CT = np.einsum("gh,huUb->guUb", C1, T1, optimize=PAIRWISE)
     s = CT.shape
     return P_up.T @ CT.reshape(s[0] * s[1] * s[2], s[3])
 
 
 def absorb_C4(C4, T3, P_dn):
     """C4'[z, c] = sum_a (C4 T3)[a=(C4.c_T4, T3.k, T3.k'), z=T3.c_C3] P_dn[c, a]."""
-    CT = np.einsum("hg,zdDh->gdDz", C4, T3)
+    CT = np.einsum("hg,zdDh->gdDz", C4, T3, optimize=PAIRWISE)
     s = CT.shape
     return CT.reshape(s[0] * s[1] * s[2], s[3]).T @ P_dn.T
 
@@ -296,41 +298,41 @@ def rdm1(envs, As, i):
     bra index t left open, divided by its trace."""
     e, A = envs[i], As[i]
     # left column: C4 T4 C1 -> [c_T3, l, l', c_T1]
-    left = np.einsum("mn,nlLa,ab->mlLb", e["C4"], e["T4"], e["C1"])
+    left = np.einsum("mn,nlLa,ab->mlLb", e["C4"], e["T4"], e["C1"], optimize=PAIRWISE)
     # right column: C2 T2 C3 -> [c_T1, r, r', c_T3]
-    right = np.einsum("ce,erRf,fg->crRg", e["C2"], e["T2"], e["C3"])
-    top = np.einsum("mlLb,buUc->mlLuUc", left, e["T1"])          # + T1
-    top = np.einsum("mlLuUc,crRg->mlLuUrRg", top, right)           # + right column
-    ring = np.einsum("mlLuUrRg,gdDm->lLuUrRdD", top, e["T3"])      # + T3 closes the ring
-    ket = np.einsum("lLuUrRdD,slurd->sLURD", ring, A)
-    rho = np.einsum("sLURD,tLURD->st", ket, A)
+    right = np.einsum("ce,erRf,fg->crRg", e["C2"], e["T2"], e["C3"], optimize=PAIRWISE)
+    top = np.einsum("mlLb,buUc->mlLuUc", left, e["T1"], optimize=PAIRWISE)          # + T1
+    top = np.einsum("mlLuUc,crRg->mlLuUrRg", top, right, optimize=PAIRWISE)           # + right column
+    ring = np.einsum("mlLuUrRg,gdDm->lLuUrRdD", top, e["T3"], optimize=PAIRWISE)      # + T3 closes the ring
+    ket = np.einsum("lLuUrRdD,slurd->sLURD", ring, A, optimize=PAIRWISE)
+    rho = np.einsum("sLURD,tLURD->st", ket, A, optimize=PAIRWISE)
     return rho / np.trace(rho)
 
 
 def _half_h_left(e, A):
     """Left half of the horizontal pair: C4 T4 C1 T1 T3 around A, A*.
     Returns [c (T1.c_C2), x (A.r), X (A*.r), k (T3.c_C3), p (ket s), q (bra s)]."""
-    t = np.einsum("mn,nlLa,ab->mlLb", e["C4"], e["T4"], e["C1"])
-    t = np.einsum("mlLb,buUc->mlLuUc", t, e["T1"])
-    t = np.einsum("kdDm,mlLuUc->kdDlLuUc", e["T3"], t)
-    t = np.einsum("kdDlLuUc,pluxd->kDLUcpx", t, A)
-    return np.einsum("kDLUcpx,qLUXD->cxXkpq", t, A)
+    t = np.einsum("mn,nlLa,ab->mlLb", e["C4"], e["T4"], e["C1"], optimize=PAIRWISE)
+    t = np.einsum("mlLb,buUc->mlLuUc", t, e["T1"], optimize=PAIRWISE)
+    t = np.einsum("kdDm,mlLuUc->kdDlLuUc", e["T3"], t, optimize=PAIRWISE)
+    t = np.einsum("kdDlLuUc,pluxd->kDLUcpx", t, A, optimize=PAIRWISE)
+    return np.einsum("kDLUcpx,qLUXD->cxXkpq", t, A, optimize=PAIRWISE)
 
 
 def _half_h_right(e, A):
     """Right half: T1 C2 T2 C3 T3 around A, A*.
     Returns [c (T1.c_C1), x (A.l), X (A*.l), k (T3.c_C4), s, t]."""
-    u = np.einsum("cvVe,ef,frRg,gh->cvVrRh", e["T1"], e["C2"], e["T2"], e["C3"])
-    u = np.einsum("cvVrRh,hwWk->cvVrRwWk", u, e["T3"])
-    u = np.einsum("cvVrRwWk,sxvrw->cVRWksx", u, A)
-    return np.einsum("cVRWksx,tXVRW->cxXkst", u, A)
+    u = np.einsum("cvVe,ef,frRg,gh->cvVrRh", e["T1"], e["C2"], e["T2"], e["C3"], optimize=PAIRWISE)
+    u = np.einsum("cvVrRh,hwWk->cvVrRwWk", u, e["T3"], optimize=PAIRWISE)
+    u = np.einsum("cvVrRwWk,sxvrw->cVRWksx", u, A, optimize=PAIRWISE)
+    return np.einsum("cVRWksx,tXVRW->cxXkst", u, A, optimize=PAIRWISE)
 
 
 def rdm2_horizontal(envs, As, i, j):
     """i = left site, j = its right neighbour; rho[(s_i s_j), (t_i t_j)]."""
     L = _half_h_left(envs[i], As[i])
     Rh = _half_h_right(envs[j], As[j])
-    rho = np.einsum("cxXkpq,cxXkst->psqt", L, Rh)
+    rho = np.einsum("cxXkpq,cxXkst->psqt", L, Rh, optimize=PAIRWISE)
     dI, dJ = As[i].shape[0], As[j].shape[0]
     rho = rho.reshape(dI * dJ, dI * dJ)
     return rho / np.trace(rho)
@@ -339,26 +341,26 @@ def rdm2_horizontal(envs, As, i, j):
 def _half_v_top(e, A):
     """Top half of the vertical pair: T4 C1 T1 C2 T2 around A, A*.
     Returns [n (T4.c_C4), y (A.d), Y (A*.d), f (T2.c_C3), s, t]."""
-    u = np.einsum("nvVa,ab,buUc,ce->nvVuUe", e["T4"], e["C1"], e["T1"], e["C2"])
-    u = np.einsum("nvVuUe,erRf->nvVuUrRf", u, e["T2"])
-    u = np.einsum("nvVuUrRf,svury->nVURfsy", u, A)
-    return np.einsum("nVURfsy,tVURY->nyYfst", u, A)
+    u = np.einsum("nvVa,ab,buUc,ce->nvVuUe", e["T4"], e["C1"], e["T1"], e["C2"], optimize=PAIRWISE)
+    u = np.einsum("nvVuUe,erRf->nvVuUrRf", u, e["T2"], optimize=PAIRWISE)
+    u = np.einsum("nvVuUrRf,svury->nVURfsy", u, A, optimize=PAIRWISE)
+    return np.einsum("nVURfsy,tVURY->nyYfst", u, A, optimize=PAIRWISE)
 
 
 def _half_v_bottom(e, A):
     """Bottom half: T2 C3 T3 C4 T4 around A, A*.
     Returns [n (T4.c_C1), y (A.u), Y (A*.u), f (T2.c_C2), p, q]."""
-    t = np.einsum("fwWg,gh,hdDk,km->fwWdDm", e["T2"], e["C3"], e["T3"], e["C4"])
-    t = np.einsum("fwWdDm,mlLn->fwWdDlLn", t, e["T4"])
-    t = np.einsum("fwWdDlLn,plywd->fWDLnpy", t, A)
-    return np.einsum("fWDLnpy,qLYWD->nyYfpq", t, A)
+    t = np.einsum("fwWg,gh,hdDk,km->fwWdDm", e["T2"], e["C3"], e["T3"], e["C4"], optimize=PAIRWISE)
+    t = np.einsum("fwWdDm,mlLn->fwWdDlLn", t, e["T4"], optimize=PAIRWISE)
+    t = np.einsum("fwWdDlLn,plywd->fWDLnpy", t, A, optimize=PAIRWISE)
+    return np.einsum("fWDLnpy,qLYWD->nyYfpq", t, A, optimize=PAIRWISE)
 
 
 def rdm2_vertical(envs, As, i, j):
     """i = bottom site, j = its top neighbour; rho[(s_i s_j), (t_i t_j)]."""
     Tp = _half_v_top(envs[j], As[j])
     Bt = _half_v_bottom(envs[i], As[i])
-    rho = np.einsum("nyYfst,nyYfpq->psqt", Tp, Bt)
+    rho = np.einsum("nyYfst,nyYfpq->psqt", Tp, Bt, optimize=PAIRWISE)
     dI, dJ = As[i].shape[0], As[j].shape[0]
     rho = rho.reshape(dI * dJ, dI * dJ)
     return rho / np.trace(rho)
@@ -397,7 +399,8 @@ def log_kappa_per_site(envs, As):
     """ln kappa per site = (1/4) ln(Z_22 Z_00 / (Z_20 Z_02)) for a 2x2 cell.
 
     Sites TL=(0,1), TR=(1,1), BL=(0,0), BR=(1,0).  Z_22: the 4 corners, the
-    8 edge tensors around the cell and its 4 double-layer sites; Z_00: the
+    8 edge tensors around the cell and its 4 double-layer sites, evaluated as
+    Tr(H_u^T H_d) of the cut through the block; Z_00: the
     four corners joined directly; Z_20: corners plus the top and bottom edge
     pairs, each T1 ket/bra leg joined to the T3 of the same column (a strip
     with no sites); Z_02: likewise with the right and left edge pairs.
@@ -411,31 +414,15 @@ def log_kappa_per_site(envs, As):
     t2a, t2b = E[TR]["T2"], E[BR]["T2"]
     t3a, t3b = E[BR]["T3"], E[BL]["T3"]
     t4a, t4b = E[BL]["T4"], E[TL]["T4"]
-    z00 = np.einsum("ab,bc,cd,da->", c1, c2, c3, c4)
+    z00 = np.einsum("ab,bc,cd,da->", c1, c2, c3, c4, optimize=PAIRWISE)
     z20 = np.einsum("ab,buUc,cvVe,ef,fg,gvVh,huUk,ka->",
-                    c1, t1a, t1b, c2, c3, t3a, t3b, c4, optimize=PAIRWISE)
+                    c1, t1a, t1b, c2, c3, t3a, t3b, c4, optimize=True)
     z02 = np.einsum("ab,bc,crRd,dsSe,ef,fg,gsSh,hrRa->",
-                    c1, c2, t2a, t2b, c3, c4, t4a, t4b, optimize=PAIRWISE)
-    # upper half: C1 T1(TL) T1(TR) C2 T2(TR), the TR and TL sites, T4(TL)
-    up = np.einsum("ab,buUc->auUc", c1, t1a)
-    up = np.einsum("auUc,cvVe->auUvVe", up, t1b)
-    up = np.einsum("auUvVe,ef->auUvVf", up, c2)
-    up = np.einsum("auUvVf,frRg->auUvVrRg", up, t2a)
-    up = np.einsum("auUvVrRg,sxvrp->auUVRgsxp", up, As[TR])
-    up = np.einsum("auUVRgsxp,sXVRP->auUgxXpP", up, As[TR])
-    up = np.einsum("auUgxXpP,hlLa->hlLuUgxXpP", up, t4b)
-    up = np.einsum("hlLuUgxXpP,tluxq->hLUgXpPtq", up, As[TL])
-    up = np.einsum("hLUgXpPtq,tLUXQ->gpPqQh", up, As[TL])
-    # lower half: T2(BR) C3 T3(BR), the BR site, T3(BL) C4 T4(BL), the BL site
-    dn = np.einsum("gwWi,ij->gwWj", t2b, c3)
-    dn = np.einsum("gwWj,jyYk->gwWyYk", dn, t3a)
-    dn = np.einsum("gwWyYk,sxpwy->gWYksxp", dn, As[BR])
-    dn = np.einsum("gWYksxp,sXPWY->gkxpXP", dn, As[BR])
-    dn = np.einsum("gkxpXP,kzZm->gxpXPzZm", dn, t3b)
-    dn = np.einsum("gxpXPzZm,mn->gxpXPzZn", dn, c4)
-    dn = np.einsum("gxpXPzZn,nlLh->gxpXPzZlLh", dn, t4a)
-    dn = np.einsum("gxpXPzZlLh,tlqxz->gpXPZLhtq", dn, As[BL])
-    dn = np.einsum("gpXPZLhtq,tLQXZ->gpPqQh", dn, As[BL])
-    z22 = np.einsum("gpPqQh,gpPqQh->", up, dn)
+                    c1, c2, t2a, t2b, c3, c4, t4a, t4b, optimize=True)
+    # Z_22 is the closed network of the block with its environment: the
+    # half systems of the cut between rows 0 and 1 at column 0 (the same
+    # four sites and environment tensors) give it as Tr(H_u^T H_d)
+    Hu, Hd = half_systems(*cut_corners(envs, As, 0, 0, 2, 2))
+    z22 = float(np.sum(Hu * Hd))
     ratio = z22 * z00 / (z20 * z02)
     return 0.25 * float(np.log(abs(ratio))), float(np.sign(ratio))

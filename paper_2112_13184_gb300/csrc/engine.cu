@@ -64,6 +64,7 @@ const FrameMaps FM;
 
 struct ctm_ctx {
     std::vector<double> last_spec;  // corner spectra at the previous ctm_spectrum_delta
+    std::vector<double> last_loop;  // loop moments at the previous ctm_loop_delta
     int d = 0, D = 0, chi = 0, N = 0, k = 0, q = 0;
     ctm_options opt{};
     cudaStream_t stream = nullptr;
@@ -624,6 +625,26 @@ ctm_status one_sweep(ctm_ctx* h) {
     return CTM_OK;
 }
 
+// Switches the handle's contractions between emulated FP64 and FP64 (every
+// buffer either needs exists from ctm_create on); the captured sweep graph
+// is dropped, the range finder's warm bases are kept.
+constexpr double FP64_REFINE_AT = 1e-8;
+ctm_status set_precision(ctm_ctx* h, int precision) {
+    if (h->opt.precision == precision) return CTM_OK;
+    if (precision == CTM_OZAKI_BF16 && !h->ozA) {
+        h->err = "handle created without the emulated-FP64 buffers";
+        return CTM_ERR_STATE;
+    }
+    CK(cudaStreamSynchronize(h->stream));
+    if (h->graph_exec) cudaGraphExecDestroy(h->graph_exec);
+    if (h->graph) cudaGraphDestroy(h->graph);
+    h->graph_exec = nullptr;
+    h->graph = nullptr;
+    for (auto& c : h->ozc) c.valid = false;
+    h->opt.precision = precision;
+    return CTM_OK;
+}
+
 ctm_status check_ready(ctm_ctx* h) {
     for (int i = 0; i < 4; ++i)
         if (!h->have_A[i]) {
@@ -671,6 +692,53 @@ ctm_status spectra(ctm_ctx* h, std::vector<double>& out) {
     out.resize(16 * (size_t)chi);
     CK(cudaMemcpyAsync(out.data(), h->spec, out.size() * sizeof(double), cudaMemcpyDeviceToHost, h->stream));
     CK(cudaStreamSynchronize(h->stream));
+    return CTM_OK;
+}
+
+// Gauge-invariant convergence measure: for the 2x2 block with bottom-left
+// site i, the corner loop L = C1(TL) C2(TR) C3(BR) C4(BL) (the network Z_00)
+// changes under a change of basis G on any chi bond only to a similar
+// matrix, so the normalised moments m_p = Tr(L^p) / Tr(L)^p, p = 2, 3, 4 (sums
+// of the p-th powers of the loop eigenvalues normalised to sum 1) do not
+// depend on the gauge the projectors leave on the chi bonds, while the
+// singular values of a single corner do.  The moments are also unchanged by
+// L -> c L, so the free overall sign each corner carries (every C is divided
+// by its own largest |entry|) drops out.  FP64 products (chi^3 each).
+// out: 4 blocks x 3 moments; NaN where Tr(L) is zero or not finite.
+ctm_status loop_moments(ctm_ctx* h, std::vector<double>& out) {
+    const int chi = h->chi;
+    const size_t C = (size_t)chi * chi;
+    double* w = h->corners;  // 16 chi^2 scratch: ta, tb, L, L2, L3, L4 per block in turn
+    double* ta = w;
+    double* tb = w + C;
+    double* L = w + 2 * C;  // L, L^2, L^3, L^4 contiguous for one traces() call
+    double tr[16];
+    out.assign(12, 0.0);
+    for (int i = 0; i < 4; ++i) {
+        const int x = i % 2, y = i / 2;
+        auto site = [](int xx, int yy) { return ((xx % 2 + 2) % 2) + 2 * ((yy % 2 + 2) % 2); };
+        const double* c1 = h->env[site(x, y + 1)][C1];
+        const double* c2 = h->env[site(x + 1, y + 1)][C2];
+        const double* c3 = h->env[site(x + 1, y)][C3];
+        const double* c4 = h->env[site(x, y)][C4];
+        CK(ctm::dgemm(false, false, chi, chi, chi, 1.0, c1, chi, c2, chi, 0.0, ta, chi, h->stream));
+        CK(ctm::dgemm(false, false, chi, chi, chi, 1.0, ta, chi, c3, chi, 0.0, tb, chi, h->stream));
+        CK(ctm::dgemm(false, false, chi, chi, chi, 1.0, tb, chi, c4, chi, 0.0, L, chi, h->stream));
+        CK(ctm::dgemm(false, false, chi, chi, chi, 1.0, L, chi, L, chi, 0.0, L + C, chi, h->stream));
+        CK(ctm::dgemm(false, false, chi, chi, chi, 1.0, L + C, chi, L, chi, 0.0, L + 2 * C, chi, h->stream));
+        CK(ctm::dgemm(false, false, chi, chi, chi, 1.0, L + C, chi, L + C, chi, 0.0, L + 3 * C, chi, h->stream));
+        CK(ctm::traces(L, chi, 4, h->scal + 4 * (i % 2), h->stream));
+        if (i % 2 == 1 || i == 3) {
+            CK(cudaMemcpyAsync(tr + 4 * (i - 1), h->scal, 8 * sizeof(double), cudaMemcpyDeviceToHost, h->stream));
+            CK(cudaStreamSynchronize(h->stream));
+        }
+    }
+    for (int i = 0; i < 4; ++i) {
+        const double t1 = tr[4 * i];
+        for (int p = 2; p <= 4; ++p)
+            out[3 * i + (p - 2)] = (t1 != 0.0 && std::isfinite(t1)) ? tr[4 * i + p - 1] / std::pow(t1, (double)p)
+                                                                   : NAN;
+    }
     return CTM_OK;
 }
 
@@ -874,6 +942,8 @@ ctm_status ctm_default_options(ctm_options* o) {
     o->seed = 0;
     o->exact_svd_max_n = 256;
     o->rsvd_warm_start = 1;
+    o->conv_measure = 0;
+    o->fp64_refine = 0;
     return CTM_OK;
 }
 
@@ -881,6 +951,7 @@ static ctm_status validate(int d, int D, const ctm_options* o) {
     if (!o || d < 1 || D < 1 || o->chi < 1 || d > 64 || D > 64) return CTM_ERR_ARG;
     if (o->precision != CTM_FP64 && o->precision != CTM_OZAKI_BF16) return CTM_ERR_ARG;
     if (o->rsvd_power_iters < 0) return CTM_ERR_ARG;
+    if (o->conv_measure != 0 && o->conv_measure != 1) return CTM_ERR_ARG;
     if (o->precision == CTM_OZAKI_BF16 && (o->ozaki_slices < 2 || o->ozaki_slices > 6)) return CTM_ERR_ARG;
     const long long N = (long long)o->chi * D * D;
     if ((long long)d * d * N * N >= (1ll << 32)) return CTM_ERR_ARG;  // index range of the kernels
@@ -1101,23 +1172,57 @@ ctm_status ctm_run(ctm_handle h, int* sweeps_done, double* last_delta) {
     if (!h) return CTM_ERR_ARG;
     CKS(check_ready(h));
     std::vector<double> prev, cur;
-    CKS(spectra(h, prev));
+    const bool loops = h->opt.conv_measure == 1;
+    auto measure = [&](std::vector<double>& v) { return loops ? loop_moments(h, v) : spectra(h, v); };
+    CKS(measure(prev));
     double delta = INFINITY;
     int n = 0;
     ctm_status st = CTM_NOT_CONVERGED;
     for (n = 1; n <= h->opt.max_sweeps; ++n) {
         CKS(one_sweep(h));
         CKS(read_flag(h));
-        CKS(spectra(h, cur));
+        CKS(measure(cur));
         delta = 0.0;
-        for (size_t i = 0; i < cur.size(); ++i) delta = std::max(delta, std::fabs(cur[i] - prev[i]));
+        for (size_t i = 0; i < cur.size(); ++i) {
+            const double x = std::fabs(cur[i] - prev[i]);
+            delta = (x != x) ? INFINITY : std::max(delta, x);
+        }
         prev.swap(cur);
         if (delta < h->opt.tol) { st = CTM_OK; break; }
+        if (h->opt.fp64_refine && h->opt.precision == CTM_OZAKI_BF16 && delta < FP64_REFINE_AT) {
+            // the emulated products' rounding keeps the measure from falling
+            // much below this: the remaining sweeps run in FP64
+            CKS(set_precision(h, CTM_FP64));
+        }
     }
     if (n > h->opt.max_sweeps) n = h->opt.max_sweeps;
     if (sweeps_done) *sweeps_done = n;
     if (last_delta) *last_delta = delta;
     return st;
+}
+
+ctm_status ctm_set_precision(ctm_handle h, int precision) {
+    if (!h || (precision != CTM_FP64 && precision != CTM_OZAKI_BF16)) return CTM_ERR_ARG;
+    return set_precision(h, precision);
+}
+
+ctm_status ctm_loop_delta(ctm_handle h, double* delta) {
+    if (!h || !delta) return CTM_ERR_ARG;
+    CKS(check_ready(h));
+    CKS(read_flag(h));
+    std::vector<double> cur;
+    CKS(loop_moments(h, cur));
+    double d = INFINITY;
+    if (h->last_loop.size() == cur.size()) {
+        d = 0.0;
+        for (size_t i = 0; i < cur.size(); ++i) {
+            const double x = std::fabs(cur[i] - h->last_loop[i]);
+            d = (x != x) ? INFINITY : std::max(d, x);  // an undefined moment never counts as converged
+        }
+    }
+    h->last_loop.swap(cur);
+    *delta = d;
+    return CTM_OK;
 }
 
 ctm_status ctm_corner_spectra(ctm_handle h, double* out_host) {

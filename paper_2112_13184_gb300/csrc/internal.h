@@ -36,6 +36,8 @@ cudaError_t scale_by_max(double* x, size_t n, const unsigned long long* maxbits,
 // *out = sum_i x[i] y[i] in a fixed order; ws: dot_ws_doubles() doubles
 size_t dot_ws_doubles();
 cudaError_t dot(const double* x, const double* y, size_t n, double* out, double* ws, cudaStream_t s);
+// out[m] = trace of the m-th n x n matrix of As (contiguous), m < nm
+cudaError_t traces(const double* As, int n, int nm, double* out, cudaStream_t s);
 // blocks x threads threads, each 8 x iters FP64 FMAs; out: blocks x threads doubles
 cudaError_t dfma_probe(double* out, int blocks, int threads, int iters, cudaStream_t s);
 // T[a,k,k',b] (chi x D x D x chi) symmetrised over (k, k') in place

@@ -384,12 +384,28 @@ __global__ void k_dfma_probe(double* __restrict__ out, int iters, double a, doub
     out[blockIdx.x * blockDim.x + threadIdx.x] = s;
 }
 
+// out[m] = trace of the n x n matrix As + m n^2, m < nm (one warp per matrix)
+__global__ void k_traces(const double* __restrict__ As, int n, int nm, double* __restrict__ out) {
+    const int m = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5), lane = threadIdx.x & 31;
+    if (m >= nm) return;
+    const double* a = As + (size_t)m * n * n;
+    double t = 0.0;
+    for (int i = lane; i < n; i += 32) t += a[(size_t)i * (n + 1)];
+    for (int o = 16; o > 0; o >>= 1) t += __shfl_xor_sync(0xffffffffu, t, o);
+    if (lane == 0) out[m] = t;
+}
+
 size_t dot_ws_doubles() { return DOT_BLOCKS; }
 cudaError_t dot(const double* x, const double* y, size_t n, double* out, double* ws, cudaStream_t s) {
     ++g_launches;
     k_dot_partial<<<DOT_BLOCKS, 256, 0, s>>>(x, y, n, ws);
     ++g_launches;
     k_dot_final<<<1, 256, 0, s>>>(ws, DOT_BLOCKS, out);
+    return cudaGetLastError();
+}
+cudaError_t traces(const double* As, int n, int nm, double* out, cudaStream_t s) {
+    ++g_launches;
+    k_traces<<<(nm + 7) / 8, 256, 0, s>>>(As, n, nm, out);
     return cudaGetLastError();
 }
 cudaError_t dfma_probe(double* out, int blocks, int threads, int iters, cudaStream_t s) {

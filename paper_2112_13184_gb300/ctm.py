@@ -36,7 +36,7 @@ class ctm_options(ctypes.Structure):
     _fields_ = [("chi", c_int), ("max_sweeps", c_int), ("tol", c_double), ("precision", c_int),
                 ("ozaki_slices", c_int), ("rsvd_oversample", c_int), ("rsvd_power_iters", c_int),
                 ("sv_cutoff_rel", c_double), ("seed", ctypes.c_uint64), ("exact_svd_max_n", c_int),
-                ("rsvd_warm_start", c_int)]
+                ("rsvd_warm_start", c_int), ("conv_measure", c_int), ("fp64_refine", c_int)]
 
 
 class ctm_profile_data(ctypes.Structure):
@@ -67,6 +67,8 @@ _sig("ctm_sweep_async", c_int, c_void_p, c_int)
 _sig("ctm_sync", c_int, c_void_p)
 _sig("ctm_batch_sweep", c_int, ctypes.POINTER(c_void_p), c_int, c_int)
 _sig("ctm_spectrum_delta", c_int, c_void_p, c_dp)
+_sig("ctm_loop_delta", c_int, c_void_p, c_dp)
+_sig("ctm_set_precision", c_int, c_void_p, c_int)
 _sig("ctm_run", c_int, c_void_p, c_ip, c_dp)
 _sig("ctm_corner_spectra", c_int, c_void_p, c_dp)
 _sig("ctm_rdm1", c_int, c_void_p, c_int, c_dp)
@@ -234,6 +236,16 @@ def ctm_fp64_peak():
     v = c_double()
     _check(_lib.ctm_fp64_peak(ctypes.byref(v)))
     return v.value
+
+
+def ctm_set_precision(h, precision):
+    _check(_lib.ctm_set_precision(h, precision), h)
+
+
+def ctm_loop_delta(h):
+    d = c_double()
+    _check(_lib.ctm_loop_delta(h, ctypes.byref(d)), h)
+    return d.value
 
 
 def ctm_run(h):
@@ -408,6 +420,9 @@ class CTMRG:
 
     def spectrum_delta(self):
         return ctm_spectrum_delta(self.h)
+
+    def loop_delta(self):
+        return ctm_loop_delta(self.h)
 
     def run(self):
         return ctm_run(self.h)

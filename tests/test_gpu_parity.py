@@ -307,3 +307,43 @@ def test_nonfinite_input_reported(ctm):
         c.sweep(1)
     assert e.value.status == ctm.CTM_ERR_NONFINITE
     c.close()
+
+
+def test_loop_delta_converges_fp64(ctm):
+    """The gauge-invariant convergence measure is large while the network
+    changes and falls below 1e-11 once the FP64 iteration has converged
+    (d=2, D=2, chi=12 Neel + 0.3 noise: the oracle converges to < 1e-12)."""
+    c = ctm.CTMRG(2, 2, 12, tol=1e-12, max_sweeps=100, conv_measure=1)
+    c.set_tensors(I.neel_tensors(2, 2, 0.3, seed=4))
+    c.set_envs(I.random_env(12, [2] * 4, seed=9))
+    c.loop_delta()
+    c.sweep(1)
+    assert c.loop_delta() > 1e-4
+    st, n, delta = c.run()
+    assert st == ctm.CTM_OK and delta < 1e-12, (st, n, delta)
+    c.loop_delta()  # reference at the fixed point (ctm_run keeps its own)
+    c.sweep(1)
+    assert c.loop_delta() < 1e-11
+    c.close()
+
+
+def test_mixed_converges_in_loop_measure(ctm):
+    """Emulated FP64 on a serving-size problem (the first request of the
+    field-scan family: D = 4, chi = 32) with the FP64 refinement: the mixed
+    sweeps bring the gauge-invariant loop measure to 1e-8, FP64 sweeps take
+    it below 1e-10, and the bond energies agree with a pure FP64 run to
+    1e-8."""
+    q = I.serving_request(0, Ds=(4,), chis=(32,))
+    out = {}
+    for prec in ("fp64", "mixed"):
+        p = ctm.CTM_OZAKI_BF16 if prec == "mixed" else ctm.CTM_FP64
+        c = ctm.CTMRG(q["d"], q["D"], q["chi"], precision=p, tol=1e-10, max_sweeps=80, conv_measure=1,
+                      fp64_refine=1)
+        c.set_tensors(q["As"])
+        c.set_envs(q["envs"])
+        st, n, delta = c.run()
+        print(f"{prec}: status {st} after {n} sweeps, loop delta {delta:.2e}")
+        assert st == ctm.CTM_OK, (prec, n, delta)
+        out[prec] = np.array([c.measure2(i, dx, dy, q["op2"]) for (i, dx, dy) in I.SQUARE_2X2_BONDS])
+        c.close()
+    assert np.max(np.abs(out["mixed"] - out["fp64"])) < 1e-8
