@@ -38,6 +38,8 @@ WORKLOADS = {
     "neel_d2_D6_chi72": "d=2, D=6, chi=72, 2x2 cell, Neel + 0.1 noise (seed 2), env seed 3",
     "neel_d2_D3_chi16": "d=2, D=3, chi=16, 2x2 cell, Neel + 0.1 noise (seed 0), env seed 1",
 }
+PRECISIONS = {"fp64": "CTM_FP64", "mixed": "CTM_OZAKI_BF16", "bf16x3": "CTM_SPLIT_BF16", "tf32x3": "CTM_3XTF32"}
+DTYPES = {"fp64": "f64", "mixed": "bf16x-slices->f64", "bf16x3": "bf16x3->f32", "tf32x3": "tf32x3->f32"}
 METRIC = "CTMRG sweeps/s at D=8,chi=128 (d=3, 2x2 cell), mixed vs FP64 @|dE|<=1e-8; p50/p99 latency"
 TRAFFIC_PROFILE = os.path.join(ROOT, "profiles", "launches_xpol_d3_D8_chi128_mixed.md")
 
@@ -48,7 +50,9 @@ def parse():
     ap.add_argument("--steps", type=int, default=3)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--precision", default="mixed", choices=["fp64", "mixed"])
+    ap.add_argument("--precision", default="mixed", choices=sorted(PRECISIONS),
+                    help="mixed: emulated FP64 (--slices BF16 slices, exact levels); bf16x3 / tf32x3: "
+                         "FP32-summed split-BF16 / 3xTF32 (precision study, not gated at 1e-8)")
     ap.add_argument("--slices", type=int, default=5)
     ap.add_argument("--workload", default="xpol_d3_D8_chi128", choices=sorted(WORKLOADS))
     ap.add_argument("--e2e-steps", type=int, default=3)
@@ -202,7 +206,7 @@ def read_traffic():
     return None
 
 
-def oz_gemm_roofline(by_op):
+def oz_gemm_roofline(by_op, tf32=False):
     """Roofline of the emulated-FP64 GEMM class (k_oz_gemm) over one sweep.
 
     Each operation tag records its tensor flops (2 M N K per BF16 slice
@@ -212,7 +216,8 @@ def oz_gemm_roofline(by_op):
     bound that dominates its summed roofline time, with the roofline-time
     fraction (sum of roofline times / measured time) beside it."""
     peaks = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
-    tc = peaks["bf16_tflops_sustained"] * 1e12
+    # TF32 slices run at the nominal TF32 / BF16 dense ratio (1.1 / 2.25 PFLOP/s)
+    tc = peaks["bf16_tflops_sustained"] * 1e12 * (1.1 / 2.25 if tf32 else 1.0)
     bw = peaks["hbm_gbs"] * 1e9
     F = B = T = t_tc = t_bw = t_roof = 0.0
     ops = {}
@@ -231,10 +236,12 @@ def oz_gemm_roofline(by_op):
     achieved = F / T / 1e12 if tensor else B / T / 1e9
     peak = tc / 1e12 if tensor else bw / 1e9
     top = dict(sorted(ops.items(), key=lambda kv: -kv[1]["ms"])[:8])
-    return {"bound": "tensor" if tensor else "hbm", "kernel": "k_oz_gemm (tcgen05 BF16 slice products)",
+    return {"bound": "tensor" if tensor else "hbm",
+            "kernel": f"k_oz_gemm (tcgen05 {'TF32' if tf32 else 'BF16'} slice products)",
             "achieved": achieved, "peak": peak, "unit": "TFLOP/s" if tensor else "GB/s",
             "frac": achieved / peak, "traffic": read_traffic(), "algorithmic_bytes": B,
-            "peak_source": ("MEASURED_PEAKS.json bf16_tflops_sustained (of measured)" if tensor
+            "peak_source": ("MEASURED_PEAKS.json bf16_tflops_sustained" + (" x 1.1/2.25 (TF32)" if tf32 else "")
+                            + " (of measured)" if tensor
                             else "MEASURED_PEAKS.json hbm_gbs (of measured)"),
             "roofline_time_frac": t_roof / T, "class_ms": T * 1e3,
             "note": ("achieved = sum over the sweep's emulated GEMMs of the algorithmic work in the "
@@ -414,7 +421,7 @@ def run_ours(args):
 
     w = I.workload(args.workload)
     d, D, chi = w["d"], w["D"], w["chi"]
-    prec = C.CTM_OZAKI_BF16 if args.precision == "mixed" else C.CTM_FP64
+    prec = getattr(C, PRECISIONS[args.precision])
     stream = torch.cuda.Stream()
     solver = C.CTMRG(d, D, chi, stream=stream, precision=prec, seed=rank, ozaki_slices=args.slices)
     solver.set_tensors(w["As"])
@@ -477,7 +484,7 @@ def run_ours(args):
     e2e_value = replica_throughput(args.e2e_steps, world, e2e_max) if args.e2e_steps > 0 else None
 
     gate = None
-    if prec == C.CTM_OZAKI_BF16 and not args.no_gate and world == 1:
+    if prec != C.CTM_FP64 and not args.no_gate and world == 1:
         gate = gate_leg(C, w, solver, stream, args.slices)
     latency = None
     if not args.no_serve and world == 1:
@@ -495,15 +502,15 @@ def run_ours(args):
                     "frac": achieved / fp64_peak if achieved else None, "traffic": None,
                     "peak_source": "ctm_fp64_peak: DFMA chains on every SM, CUDA events (of measured)"}
         else:
-            roof = oz_gemm_roofline(by_op)
+            roof = oz_gemm_roofline(by_op, tf32=prec == C.CTM_3XTF32)
         total_ms = sum(p["ms"] for p in prof.values())
         line = {
             "metric": METRIC, "value": value, "unit": "sweeps/s", "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": ms_max / args.steps, "higher_is_better": True,
-            "scaling": "weak", "vs_baseline": None, "dtype": "f64" if prec == C.CTM_FP64 else "bf16x-slices->f64",
+            "scaling": "weak", "vs_baseline": None, "dtype": DTYPES[args.precision],
             "data": "synthetic",
             "config": {"workload": args.workload, "desc": WORKLOADS[args.workload], "precision": args.precision,
-                       "slices": args.slices if prec != C.CTM_FP64 else None,
+                       "slices": {"mixed": args.slices, "bf16x3": 3, "tf32x3": 2}.get(args.precision),
                        "parallelism": f"replicas x{world}",
                        "l2": "working set per sweep (N x N corners, 537 MB each) exceeds the 129 MB L2"},
             "roofline": roof,

@@ -66,11 +66,21 @@ typedef enum {
     CTM_ERR_STATE = -6       /* call out of order (e.g. no tensors set)           */
 } ctm_status;
 
+/* How the contractions (enlarged corners, range-finder and projector
+ * applies, absorption) are computed; the QR, the SVD truncation and the
+ * normalisation stay FP64 in every mode.  The tensor-core modes cut every
+ * row of op(A) and column of op(B), scaled by a power of two, into digit
+ * slices and multiply the slices on tcgen05. */
 typedef enum {
-    CTM_FP64 = 0,        /* every contraction in FP64 (CUDA-core DFMA)             */
-    CTM_OZAKI_BF16 = 1   /* contractions as exact BF16 slice products on the
-                            tensor cores (tcgen05), emulating FP64; QR, SVD and
-                            normalisation stay FP64                               */
+    CTM_FP64 = 0,        /* FP64 on the CUDA cores (DFMA)                          */
+    CTM_SPLIT_BF16 = 1,  /* 3 BF16 slices (base-256 digits), every product of
+                            levels <= 2 accumulated in FP32 over all of K      */
+    CTM_3XTF32 = 2,      /* 2 TF32 slices (base-2^11 digits), hi*hi + hi*lo +
+                            lo*hi accumulated in FP32 over all of K             */
+    CTM_OZAKI_INT8 = 3,  /* INT8 slices: not built (CTM_ERR_ARG)                 */
+    CTM_OZAKI_BF16 = 4   /* emulated FP64: ozaki_slices BF16 slices; levels 0
+                            and 1 summed exactly, levels >= 2 in FP32 per 256 of
+                            K, the whole sum exact in int64                     */
 } ctm_precision;
 
 typedef struct {
@@ -92,7 +102,7 @@ typedef struct {
     int conv_measure;       /* ctm_run's convergence measure: 0 = the normalised
                                corner spectra (ctm_spectrum_delta), 1 = the
                                gauge-invariant loop moments (ctm_loop_delta)   */
-    int fp64_refine;        /* != 0 with CTM_OZAKI_BF16: once ctm_run's measure
+    int fp64_refine;        /* != 0 with a tensor-core mode: once ctm_run's measure
                                falls below 1e-8 (about where the emulated
                                products' rounding holds it) the handle switches
                                to FP64 contractions for the remaining sweeps and
@@ -326,6 +336,19 @@ size_t ctm_gemm_ozaki_workspace_bytes(int M, int N, int K, int slices);
 ctm_status ctm_gemm_ozaki(int transA, int transB, int M, int N, int K, double alpha, const double* A, int lda,
                           const double* B, int ldb, double beta, double* C, int ldc, int slices, void* ws,
                           void* stream);
+
+/* C[M,N] = alpha op(A) op(B) + beta C like ctm_dgemm, as the FP32-accumulated
+ * tensor-core products of `precision` = CTM_SPLIT_BF16 (3 BF16 slices) or
+ * CTM_3XTF32 (2 TF32 slices).  Error ~ 2^-24 K max|row of op(A)| max|col of
+ * op(B)| from the FP32 accumulation; products whose digits fit one slice
+ * and whose sums stay below 2^24 units are exact.  ws:
+ * ctm_gemm_split_workspace_bytes(precision, M, N, K) bytes, its first int set
+ * non-zero if a bounded wait inside the kernel gave up.  Not synchronised.
+ * (No counterpart in the paper: the precision study's kernel-level entry.) */
+size_t ctm_gemm_split_workspace_bytes(int precision, int M, int N, int K);
+ctm_status ctm_gemm_split(int precision, int transA, int transB, int M, int N, int K, double alpha,
+                          const double* A, int lda, const double* B, int ldb, double beta, double* C, int ldc,
+                          void* ws, void* stream);
 
 /* ctm_svd without a caller workspace and without allocating (the paper has
  * no counterpart; this is a deployment aid).  For callers that cannot call

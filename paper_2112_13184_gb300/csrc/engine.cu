@@ -74,6 +74,7 @@ struct ctm_ctx {
     unsigned env_set = 0;  // bit (site*8 + which)
     uint64_t rng_counter = 0;
     long long jacobi_capped = 0;  // read_flag calls that saw a capped Jacobi SVD
+    int tc_prec = CTM_FP64;       // the tensor-core precision the handle was created with
 
     std::vector<void*> allocs;
     double* A[4][4] = {};     // [site][rotation]  [s,l,u,r,d]
@@ -175,15 +176,38 @@ std::vector<std::array<long long, 3>> gemm_shapes(int d, int D, int chi, int k) 
             {k, k, N},          {N, k, k}};
 }
 
+// Tensor-core contraction scheme of a precision: -1 FP64 (DFMA), 0 exact-level
+// emulated FP64 (CTM_OZAKI_BF16), 1 split-BF16, 2 3xTF32 (both FP32-accumulated)
+int tc_mode_of(int precision) {
+    switch (precision) {
+        case CTM_OZAKI_BF16: return 0;
+        case CTM_SPLIT_BF16: return 1;
+        case CTM_3XTF32: return 2;
+        default: return -1;
+    }
+}
+// operand slices per element of a scheme
+int tc_slices_of(const ctm_options& o) {
+    switch (tc_mode_of(o.precision)) {
+        case 0: return o.ozaki_slices;
+        case 1: return 3;
+        case 2: return 2;
+        default: return 0;
+    }
+}
+size_t tc_split_bytes(int R, int K, int mode, int s) {
+    return mode == 2 ? ctm::oz_split_tf32_bytes(R, K) : ctm::oz_split_bytes(R, K, s);
+}
+
 struct OzBounds {
     size_t a = 0, b = 0, w = 0;
 };
-OzBounds oz_bounds(int d, int D, int chi, int k, int s) {
+OzBounds oz_bounds(int d, int D, int chi, int k, int s, int mode) {
     OzBounds z;
     for (const auto& sh : gemm_shapes(d, D, chi, k)) {
-        z.a = std::max(z.a, ctm::oz_split_bytes((int)sh[0], (int)sh[2], s));
-        z.b = std::max(z.b, ctm::oz_split_bytes((int)sh[1], (int)sh[2], s));
-        z.w = std::max(z.w, ctm::oz_gemm_ws_bytes((int)sh[0], (int)sh[1], (int)sh[2], s));
+        z.a = std::max(z.a, tc_split_bytes((int)sh[0], (int)sh[2], mode, s));
+        z.b = std::max(z.b, tc_split_bytes((int)sh[1], (int)sh[2], mode, s));
+        z.w = std::max(z.w, ctm::oz_gemm_ws_bytes((int)sh[0], (int)sh[1], (int)sh[2], s, mode));
     }
     return z;
 }
@@ -212,9 +236,11 @@ size_t footprint(int d, int D, const ctm_options& o) {
     bytes += qr_ws_bytes(N, k) + svd_ws_bytes(k) + svals_ws_bytes(chi, 16);
     bytes += 64 * sizeof(unsigned long long) + 64 + 64 * 256;
     bytes += sizeof(double) * (ctm::dot_ws_doubles() + 8);
-    if (o.precision == CTM_OZAKI_BF16) {
-        const OzBounds z = oz_bounds(d, D, chi, k, o.ozaki_slices);
-        bytes += z.a + z.b + z.w + 3 * 256 + 8 * ctm::oz_split_bytes(N, N, o.ozaki_slices);
+    const int mode = tc_mode_of(o.precision);
+    if (mode >= 0) {
+        const int s = tc_slices_of(o);
+        const OzBounds z = oz_bounds(d, D, chi, k, s, mode);
+        bytes += z.a + z.b + z.w + 3 * 256 + 8 * tc_split_bytes(N, N, mode, s);
     }
     return bytes;
 }
@@ -302,9 +328,10 @@ void prof_collect(ctm_ctx* h) {
 // algorithmic bytes are the BF16 slices of both operands (K padded to 8) and
 // the FP64 output (read too when beta != 0).
 double oz_flops(int M, int N, int K, int s) { return 2.0 * M * N * K * (s * (s + 1) / 2); }
-double oz_bytes(int M, int N, int K, int s, bool beta) {
-    const double K8 = (double)((K + 7) & ~7);
-    return 2.0 * s * ((double)M * K8 + (double)N * K8) + 8.0 * M * N * (beta ? 2.0 : 1.0);
+double oz_bytes(int M, int N, int K, int s, bool beta, int mode = 0) {
+    const double Kp = mode == 2 ? (double)((K + 3) & ~3) : (double)((K + 7) & ~7);
+    const double esz = mode == 2 ? 4.0 : 2.0;  // TF32 slices are stored as FP32
+    return esz * s * ((double)M * Kp + (double)N * Kp) + 8.0 * M * N * (beta ? 2.0 : 1.0);
 }
 void slices_written(ctm_ctx* h, const double* p) {
     for (auto& c : h->ozc)
@@ -316,10 +343,23 @@ int slice_slot(ctm_ctx* h, const double* A, bool tA, int M, int K) {
         if (A == h->E[c]) return 2 * c + (tA ? 1 : 0);
     return -1;
 }
-ctm_status split_(ctm_ctx* h, const double* X, int R, int K, long long rs, long long cs, void* dst) {
+// operand slices of the handle's scheme for an R x K operand on strided views
+ctm_status split_v(ctm_ctx* h, const double* X, int R, int K, const OzView& rv, const OzView& kv, void* dst) {
+    const int mode = tc_mode_of(h->opt.precision), s = tc_slices_of(h->opt);
     const size_t ev = prof_begin(h);
-    CK(ctm::oz_split(X, R, K, rs, cs, h->opt.ozaki_slices, dst, h->stream));
-    prof_end(h, ev, P_SPLIT, 0.0, (8.0 + 2.0 * h->opt.ozaki_slices) * (double)R * K);
+    if (mode == 2) CK(ctm::oz_split_tf32(X, R, K, rv, kv, dst, h->stream));
+    else CK(ctm::oz_split_view(X, R, K, rv, kv, s, dst, h->stream));
+    prof_end(h, ev, P_SPLIT, 0.0, (8.0 + (mode == 2 ? 8.0 : 2.0 * s)) * (double)R * K);
+    return CTM_OK;
+}
+ctm_status split_(ctm_ctx* h, const double* X, int R, int K, long long rs, long long cs, void* dst) {
+    if (tc_mode_of(h->opt.precision) == 2) {
+        const OzView rv{1, {R, 1, 1, 1}, {rs, 0, 0, 0}}, kv{1, {K, 1, 1, 1}, {cs, 0, 0, 0}};
+        return split_v(h, X, R, K, rv, kv, dst);
+    }
+    const size_t ev = prof_begin(h);
+    CK(ctm::oz_split(X, R, K, rs, cs, tc_slices_of(h->opt), dst, h->stream));
+    prof_end(h, ev, P_SPLIT, 0.0, (8.0 + 2.0 * tc_slices_of(h->opt)) * (double)R * K);
     return CTM_OK;
 }
 
@@ -329,10 +369,11 @@ ctm_status gemm(ctm_ctx* h, bool tA, bool tB, int M, int N, int K, const double*
     const double flops = 2.0 * M * N * K;
     const double bytes = 8.0 * ((double)M * K + (double)K * N + (double)M * N);
     // a matrix-vector product gains nothing from 128-wide tensor tiles
-    if (h->opt.precision == CTM_OZAKI_BF16 && M > 0 && N > 1 && K > 0) {
-        const int s = h->opt.ozaki_slices;
-        if (ctm::oz_split_bytes(M, K, s) > h->ozA_n || ctm::oz_split_bytes(N, K, s) > h->ozB_n ||
-            ctm::oz_gemm_ws_bytes(M, N, K, s) > h->ozW_n) {
+    const int mode = tc_mode_of(h->opt.precision);
+    if (mode >= 0 && M > 0 && N > 1 && K > 0) {
+        const int s = tc_slices_of(h->opt);
+        if (tc_split_bytes(M, K, mode, s) > h->ozA_n || tc_split_bytes(N, K, mode, s) > h->ozB_n ||
+            ctm::oz_gemm_ws_bytes(M, N, K, s, mode) > h->ozW_n) {
             h->err = "emulated GEMM: shape outside the handle's workspace";
             return CTM_ERR_STATE;
         }
@@ -345,8 +386,9 @@ ctm_status gemm(ctm_ctx* h, bool tA, bool tB, int M, int N, int K, const double*
         }
         CKS(split_(h, B, N, K, tB ? ldb : 1, tB ? 1 : ldb, h->ozB));
         const size_t ev = prof_begin(h);
-        CK(ctm::oz_gemm(M, N, K, s, sa, h->ozB, 1.0, beta, C, ldc, h->ozW, h->ozW_n, h->flag + 1, h->stream));
-        prof_end(h, ev, P_GEMM, oz_flops(M, N, K, s), oz_bytes(M, N, K, s, beta != 0.0));
+        CK(ctm::oz_gemm(M, N, K, s, sa, h->ozB, 1.0, beta, C, ldc, h->ozW, h->ozW_n, h->flag + 1, h->stream,
+                        mode));
+        prof_end(h, ev, P_GEMM, oz_flops(M, N, K, s), oz_bytes(M, N, K, s, beta != 0.0, mode));
     } else {
         const size_t ev = prof_begin(h);
         CK(ctm::dgemm(tA, tB, M, N, K, 1.0, A, lda, B, ldb, beta, C, ldc, h->stream, h->splitk, h->splitk_n));
@@ -361,22 +403,18 @@ ctm_status gemm_v(ctm_ctx* h, int M, int N, int K, const double* A, const OzView
                   const double* B, const OzView& bn, const OzView& bk, double* C, const OzView& cr,
                   const OzView& cc) {
     slices_written(h, C);
-    const int s = h->opt.ozaki_slices;
-    if (ctm::oz_split_bytes(M, K, s) > h->ozA_n || ctm::oz_split_bytes(N, K, s) > h->ozB_n ||
-        ctm::oz_gemm_ws_bytes(M, N, K, s) > h->ozW_n) {
+    const int mode = tc_mode_of(h->opt.precision), s = tc_slices_of(h->opt);
+    if (tc_split_bytes(M, K, mode, s) > h->ozA_n || tc_split_bytes(N, K, mode, s) > h->ozB_n ||
+        ctm::oz_gemm_ws_bytes(M, N, K, s, mode) > h->ozW_n) {
         h->err = "emulated GEMM: shape outside the handle's workspace";
         return CTM_ERR_STATE;
     }
-    size_t ev = prof_begin(h);
-    CK(ctm::oz_split_view(A, M, K, ar, ak, s, h->ozA, h->stream));
-    prof_end(h, ev, P_SPLIT, 0.0, (8.0 + 2.0 * s) * (double)M * K);
-    ev = prof_begin(h);
-    CK(ctm::oz_split_view(B, N, K, bn, bk, s, h->ozB, h->stream));
-    prof_end(h, ev, P_SPLIT, 0.0, (8.0 + 2.0 * s) * (double)N * K);
-    ev = prof_begin(h);
+    CKS(split_v(h, A, M, K, ar, ak, h->ozA));
+    CKS(split_v(h, B, N, K, bn, bk, h->ozB));
+    const size_t ev = prof_begin(h);
     CK(ctm::oz_gemm_view(M, N, K, s, h->ozA, h->ozB, 1.0, 0.0, C, cr, cc, h->ozW, h->ozW_n, h->flag + 1,
-                         h->stream));
-    prof_end(h, ev, P_GEMM, oz_flops(M, N, K, s), oz_bytes(M, N, K, s, false));
+                         h->stream, mode));
+    prof_end(h, ev, P_GEMM, oz_flops(M, N, K, s), oz_bytes(M, N, K, s, false, mode));
     return CTM_OK;
 }
 
@@ -416,7 +454,7 @@ ctm_status corner_core(ctm_ctx* h, const double* X1, const double* Tp, const dou
     const char* outer = h->tag;
     const std::string t2 = std::string(outer) + ".X2", t3 = std::string(outer) + ".X3",
                       t4 = std::string(outer) + ".X4";
-    if (h->opt.precision == CTM_OZAKI_BF16 && !open) {
+    if (tc_mode_of(h->opt.precision) >= 0 && !open) {
         // Tensor-core path.  Every permutation is folded into operand views and
         // output layouts, chosen so that both large intermediates are plain
         // K-contiguous row matrices (single-pass slicing) and the epilogue
@@ -631,8 +669,8 @@ ctm_status one_sweep(ctm_ctx* h) {
 constexpr double FP64_REFINE_AT = 1e-8;
 ctm_status set_precision(ctm_ctx* h, int precision) {
     if (h->opt.precision == precision) return CTM_OK;
-    if (precision == CTM_OZAKI_BF16 && !h->ozA) {
-        h->err = "handle created without the emulated-FP64 buffers";
+    if (precision != CTM_FP64 && precision != h->tc_prec) {
+        h->err = "a handle switches only between FP64 and the tensor-core precision it was created with";
         return CTM_ERR_STATE;
     }
     CK(cudaStreamSynchronize(h->stream));
@@ -949,7 +987,7 @@ ctm_status ctm_default_options(ctm_options* o) {
 
 static ctm_status validate(int d, int D, const ctm_options* o) {
     if (!o || d < 1 || D < 1 || o->chi < 1 || d > 64 || D > 64) return CTM_ERR_ARG;
-    if (o->precision != CTM_FP64 && o->precision != CTM_OZAKI_BF16) return CTM_ERR_ARG;
+    if (o->precision != CTM_FP64 && tc_mode_of(o->precision) < 0) return CTM_ERR_ARG;
     if (o->rsvd_power_iters < 0) return CTM_ERR_ARG;
     if (o->conv_measure != 0 && o->conv_measure != 1) return CTM_ERR_ARG;
     if (o->precision == CTM_OZAKI_BF16 && (o->ozaki_slices < 2 || o->ozaki_slices > 6)) return CTM_ERR_ARG;
@@ -969,6 +1007,10 @@ ctm_status ctm_create(int Lx, int Ly, int d, int D, const ctm_options* o, void* 
     *out = nullptr;
     if (Lx != 2 || Ly != 2) {
         g_err = "ctm_create: only the 2x2 unit cell (Lx = Ly = 2) is built";
+        return CTM_ERR_ARG;
+    }
+    if (o && o->precision == CTM_OZAKI_INT8) {
+        g_err = "ctm_create: CTM_OZAKI_INT8 is not built (INT8 tensor-core slices)";
         return CTM_ERR_ARG;
     }
     if (validate(d, D, o) != CTM_OK) {
@@ -1028,8 +1070,10 @@ ctm_status ctm_create(int Lx, int Ly, int d, int D, const ctm_options* o, void* 
     if (st == CTM_OK) st = allocd(h, &h->scal, 8);
     if (o->rsvd_warm_start && h->k < h->N)
         for (int c = 0; c < 16 && st == CTM_OK; ++c) st = allocd(h, &h->warmV[c], z.Nk);
-    if (st == CTM_OK && o->precision == CTM_OZAKI_BF16) {
-        const OzBounds zb = oz_bounds(d, D, h->chi, h->k, o->ozaki_slices);
+    const int tmode = tc_mode_of(o->precision), tsl = tc_slices_of(*o);
+    if (tmode >= 0) h->tc_prec = o->precision;
+    if (st == CTM_OK && tmode >= 0) {
+        const OzBounds zb = oz_bounds(d, D, h->chi, h->k, tsl, tmode);
         h->ozA_n = zb.a;
         h->ozB_n = zb.b;
         h->ozW_n = std::max<size_t>(zb.w, 256);
@@ -1039,7 +1083,7 @@ ctm_status ctm_create(int Lx, int Ly, int d, int D, const ctm_options* o, void* 
         for (int c = 0; c < 8 && st == CTM_OK; ++c) {
             h->ozc[c].ptr = h->E[c / 2];
             h->ozc[c].trans = (c & 1) != 0;
-            st = alloc(h, &h->ozc[c].buf, ctm::oz_split_bytes(h->N, h->N, o->ozaki_slices));
+            st = alloc(h, &h->ozc[c].buf, tc_split_bytes(h->N, h->N, tmode, tsl));
         }
     }
     if (st != CTM_OK) {
@@ -1189,7 +1233,7 @@ ctm_status ctm_run(ctm_handle h, int* sweeps_done, double* last_delta) {
         }
         prev.swap(cur);
         if (delta < h->opt.tol) { st = CTM_OK; break; }
-        if (h->opt.fp64_refine && h->opt.precision == CTM_OZAKI_BF16 && delta < FP64_REFINE_AT) {
+        if (h->opt.fp64_refine && tc_mode_of(h->opt.precision) >= 0 && delta < FP64_REFINE_AT) {
             // the emulated products' rounding keeps the measure from falling
             // much below this: the remaining sweeps run in FP64
             CKS(set_precision(h, CTM_FP64));
@@ -1202,7 +1246,7 @@ ctm_status ctm_run(ctm_handle h, int* sweeps_done, double* last_delta) {
 }
 
 ctm_status ctm_set_precision(ctm_handle h, int precision) {
-    if (!h || (precision != CTM_FP64 && precision != CTM_OZAKI_BF16)) return CTM_ERR_ARG;
+    if (!h || (precision != CTM_FP64 && tc_mode_of(precision) < 0)) return CTM_ERR_ARG;
     return set_precision(h, precision);
 }
 
@@ -1381,6 +1425,43 @@ ctm_status ctm_gemm_ozaki(int transA, int transB, int M, int N, int K, double al
                          ctm::oz_gemm_ws_bytes(M, N, K, slices), err, st);
     if (e != cudaSuccess) {
         g_err = std::string("ctm_gemm_ozaki: ") + cudaGetErrorString(e);
+        return CTM_ERR_CUDA;
+    }
+    return CTM_OK;
+}
+
+size_t ctm_gemm_split_workspace_bytes(int precision, int M, int N, int K) {
+    const int mode = tc_mode_of(precision);
+    if (M <= 0 || N <= 0 || K <= 0 || (mode != 1 && mode != 2)) return 0;
+    const int s = mode == 1 ? 3 : 2;
+    return 256 + tc_split_bytes(M, K, mode, s) + tc_split_bytes(N, K, mode, s) + ctm::oz_gemm_ws_bytes(M, N, K, s, mode);
+}
+
+ctm_status ctm_gemm_split(int precision, int transA, int transB, int M, int N, int K, double alpha, const double* A,
+                          int lda, const double* B, int ldb, double beta, double* C, int ldc, void* ws, void* stream) {
+    const int mode = tc_mode_of(precision);
+    if ((mode != 1 && mode != 2) || M < 0 || N < 0 || K <= 0 || (M && N && (!A || !B || !C || !ws)))
+        return CTM_ERR_ARG;
+    if (!M || !N) return CTM_OK;
+    const int s = mode == 1 ? 3 : 2;
+    cudaStream_t st = (cudaStream_t)stream;
+    char* w = (char*)ws;
+    int* err = (int*)w;
+    void* sa = w + 256;
+    void* sb = (char*)sa + tc_split_bytes(M, K, mode, s);
+    void* part = (char*)sb + tc_split_bytes(N, K, mode, s);
+    const OzView ar{1, {M, 1, 1, 1}, {transA ? 1 : lda, 0, 0, 0}}, ak{1, {K, 1, 1, 1}, {transA ? lda : 1, 0, 0, 0}};
+    const OzView bn{1, {N, 1, 1, 1}, {transB ? ldb : 1, 0, 0, 0}}, bk{1, {K, 1, 1, 1}, {transB ? 1 : ldb, 0, 0, 0}};
+    cudaError_t e = cudaMemsetAsync(err, 0, sizeof(int), st);
+    if (e == cudaSuccess)
+        e = mode == 2 ? ctm::oz_split_tf32(A, M, K, ar, ak, sa, st) : ctm::oz_split_view(A, M, K, ar, ak, s, sa, st);
+    if (e == cudaSuccess)
+        e = mode == 2 ? ctm::oz_split_tf32(B, N, K, bn, bk, sb, st) : ctm::oz_split_view(B, N, K, bn, bk, s, sb, st);
+    if (e == cudaSuccess)
+        e = ctm::oz_gemm(M, N, K, s, sa, sb, alpha, beta, C, ldc, part, ctm::oz_gemm_ws_bytes(M, N, K, s, mode), err,
+                         st, mode);
+    if (e != cudaSuccess) {
+        g_err = std::string("ctm_gemm_split: ") + cudaGetErrorString(e);
         return CTM_ERR_CUDA;
     }
     return CTM_OK;

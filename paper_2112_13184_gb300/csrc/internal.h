@@ -79,14 +79,20 @@ cudaError_t oz_split(const double* X, int R, int K, long long rs, long long cs, 
 // element (r, k) at X[view(rv, r) + view(kv, k)]
 cudaError_t oz_split_view(const double* X, int R, int K, const OzView& rv, const OzView& kv, int s, void* buf,
                           cudaStream_t st);
+// TF32 operand slices of 3xTF32 (two FP32-stored TF32 slices per element)
+size_t oz_split_tf32_bytes(int R, int K);
+cudaError_t oz_split_tf32(const double* X, int R, int K, const OzView& rv, const OzView& kv, void* buf,
+                          cudaStream_t st);
 // C[M,N] = alpha A B + beta C from split A (M rows) and split B (N rows = columns of B).
-size_t oz_gemm_ws_bytes(int M, int N, int K, int s);
+// mode 0: exact-level emulated FP64 (s slices); 1: split-BF16, FP32 accumulation
+// (s = 3 BF16 slices); 2: 3xTF32, FP32 accumulation (s = 2 TF32 slices)
+size_t oz_gemm_ws_bytes(int M, int N, int K, int s, int mode = 0);
 cudaError_t oz_gemm(int M, int N, int K, int s, const void* Asplit, const void* Bsplit, double alpha, double beta,
-                    double* C, int ldc, void* ws, size_t ws_bytes, int* err, cudaStream_t st);
+                    double* C, int ldc, void* ws, size_t ws_bytes, int* err, cudaStream_t st, int mode = 0);
 // C written at C[view(out_r, m) + view(out_c, n)]
 cudaError_t oz_gemm_view(int M, int N, int K, int s, const void* Asplit, const void* Bsplit, double alpha,
                          double beta, double* C, const OzView& out_r, const OzView& out_c, void* ws, size_t ws_bytes,
-                         int* err, cudaStream_t st);
+                         int* err, cudaStream_t st, int mode = 0);
 
 // Failure-detection check of the bounded mbarrier wait used by the tensor-core
 // GEMM: one thread waits at most limit_cycles on a barrier that receives an

@@ -171,6 +171,21 @@ __device__ __forceinline__ double assemble(int S0, int S1, float F, int escale) 
     return i64_ldexp(Z, escale - 28);
 }
 
+// f 2^E as an FP64 number for an FP32 f (the accumulator of the FP32-
+// accumulated modes), built from the bit pattern: the exponent is rebiased
+// and the 23-bit significand widened, integer instructions only.
+__device__ __forceinline__ double f32_scaled(float f, int E) {
+    const unsigned b = __float_as_uint(f);
+    const int ex = (int)((b >> 23) & 0xff);
+    if (ex == 0) return 0.0;                                      // zero or FP32 denormal
+    if (ex == 255) return __longlong_as_double(0x7ff8000000000000ll);  // Inf/NaN accumulator
+    const int be = ex - 127 + 1023 + E;
+    if (be <= 0 || be >= 2047) return ldexp((double)f, E);        // outside the normal FP64 range
+    return __longlong_as_double((long long)(((unsigned long long)(b >> 31) << 63) |
+                                            ((unsigned long long)be << 52) |
+                                            ((unsigned long long)(b & 0x7fffffu) << 29)));
+}
+
 // ---------------------------------------------------------------------------
 // slicing
 // ---------------------------------------------------------------------------
@@ -336,6 +351,58 @@ __global__ void k_split_cols(const double* __restrict__ X, int R, int K, int K8,
     if (k < K8)
         for (int rr = 0; rr < 32 && r0 + rr < R; ++rr)
             for (int t = 0; t < s; ++t) out[t * plane + (size_t)(r0 + rr) * K8 + k] = tile[w][t][rr][lane];
+}
+
+// round(x 2^(nbits - e)) as an integer, |x| <= 2^e (integer operations on the
+// FP64 bit pattern, like digits())
+__device__ __forceinline__ long long scaled_round(double x, int e, int nbits) {
+    const unsigned long long b = (unsigned long long)__double_as_longlong(x);
+    int ex = (int)((b >> 52) & 0x7ff);
+    unsigned long long mant = b & ((1ull << 52) - 1);
+    if (ex == 0) ex = 1;
+    else mant |= 1ull << 52;
+    const int shift = ex - 1075 + nbits - e;
+    long long Y;
+    if (mant == 0) Y = 0;
+    else if (shift >= 0) Y = (long long)(mant << shift);
+    else {
+        const int sh = -shift;
+        Y = sh >= 54 ? 0 : (long long)((mant + (1ull << (sh - 1))) >> sh);
+    }
+    return (b >> 63) ? -Y : Y;
+}
+
+// TF32 slices for 3xTF32: round(x 2^(22 - e)) = 2048 d0 + d1 with d1 in
+// [-1024, 1023] and |d0| <= 2048; slice 0 = d0, slice 1 = d1 2^-11, each
+// with at most 11 significant bits (exact in TF32), stored as FP32
+// [2][R][K4].  One thread per row and 4 consecutive k (one 16-byte store per
+// slice); general strided views; row maxima from k_rowmax_cols.
+__global__ void k_split_tf32(const double* __restrict__ X, int R, int K, int K4, View rv, View kv,
+                             const unsigned long long* __restrict__ maxbits, float* __restrict__ out,
+                             int* __restrict__ ex) {
+    const long long tid = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+    const int nq = K4 / 4;
+    const long long r = tid / nq;
+    const int kq = (int)(tid - r * nq);
+    if (r >= R) return;
+    const int e = row_exponent(__longlong_as_double((long long)maxbits[r]));
+    if (kq == 0) ex[r] = e;
+    const long long roff = view_offset32(rv, (unsigned)r);
+    float s0[4], s1[4];
+    const float lo_scale = __int_as_float((127 - 11) << 23);  // 2^-11
+#pragma unroll
+    for (int u = 0; u < 4; ++u) {
+        const int k = 4 * kq + u;
+        const double x = k < K ? X[roff + view_offset32(kv, (unsigned)k)] : 0.0;
+        const int y = (int)scaled_round(x, e, 22);  // |y| <= 2^22
+        const int hi = (y + 1024) >> 11;
+        s0[u] = small_int_f32(hi);
+        s1[u] = small_int_f32(y - (hi << 11)) * lo_scale;
+    }
+    const size_t plane = (size_t)R * K4;
+    float* o = out + (size_t)r * K4 + 4 * kq;
+    *reinterpret_cast<float4*>(o) = make_float4(s0[0], s0[1], s0[2], s0[3]);
+    *reinterpret_cast<float4*>(o + plane) = make_float4(s1[0], s1[1], s1[2], s1[3]);
 }
 
 // ---------------------------------------------------------------------------
@@ -562,6 +629,15 @@ __device__ __forceinline__ void tc_mma(uint32_t d_tmem, uint64_t a_desc, uint64_
         "l"(a_desc), "l"(b_desc), "r"(idesc), "r"(accumulate)
         : "memory");
 }
+__device__ __forceinline__ void tc_mma_tf32(uint32_t d_tmem, uint64_t a_desc, uint64_t b_desc, uint32_t idesc,
+                                            uint32_t accumulate) {
+    asm volatile(
+        "{\n\t.reg .pred p;\n\t"
+        "setp.ne.b32 p, %4, 0;\n\t"
+        "tcgen05.mma.cta_group::1.kind::tf32 [%0], %1, %2, %3, p;\n\t}" ::"r"(d_tmem),
+        "l"(a_desc), "l"(b_desc), "r"(idesc), "r"(accumulate)
+        : "memory");
+}
 __device__ __forceinline__ void tc_commit(uint64_t* bar) {
     asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
                      smem_u32(bar))
@@ -618,13 +694,19 @@ struct GemmArgs {
 // ONE: every CTA's K range is a single chunk (every corner product), so no
 // sum is carried across chunks; a separate instantiation keeps the
 // multi-chunk sums' registers out of that path.
-template <int NB16, bool ONE>
+// MODE 0: exact-level emulated FP64 (above).  MODE 1: split-BF16 -- the same
+// BF16 digit slices, every product of levels <= s-1 accumulated in one FP32
+// accumulator over all of K.  MODE 2: 3xTF32 -- two TF32 slices (base-2^11
+// digits), hi*hi + hi*lo + lo*hi on kind::tf32 into one FP32 accumulator.
+// Modes 1 and 2 run without split-K and read TMEM once per tile.
+template <int NB16, bool ONE, int MODE>
 __global__ void __launch_bounds__(THREADS, 1)
     k_oz_gemm(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB, const GemmArgs g) {
     constexpr int BN = 16 * NB16;
     constexpr int NBG = (NB16 + 2) / 3;  // 16-column blocks per epilogue warp
-    constexpr uint32_t TMEM_COLS = (3 * BN <= 32) ? 32 : (3 * BN <= 64) ? 64 : (3 * BN <= 128) ? 128
-                                   : (3 * BN <= 256) ? 256 : 512;
+    constexpr int NACC = MODE == 0 ? 3 : 1;  // TMEM accumulators of BN columns
+    constexpr uint32_t TMEM_COLS = (NACC * BN <= 32) ? 32 : (NACC * BN <= 64) ? 64 : (NACC * BN <= 128) ? 128
+                                   : (NACC * BN <= 256) ? 256 : 512;
     extern __shared__ uint8_t smem_raw[];
     const uint32_t raw = smem_u32(smem_raw);
     const uint32_t base = (raw + 1023u) & ~1023u;
@@ -688,7 +770,7 @@ __global__ void __launch_bounds__(THREADS, 1)
                     }
                     uint8_t* sa = sbase + (size_t)st * g.stage_bytes;
                     mbar_expect_tx(&full[st], g.stage_bytes);
-                    const int kc = (kb0 + i) * BK;
+                    const int kc = (kb0 + i) * (MODE == 2 ? BK / 2 : BK);  // 64 bytes of K per stage
                     tma_load_3d(sa, &tmA, kc, m0, 0, &full[st]);
                     tma_load_3d(sa + g.a_bytes, &tmB, kc, n0, 0, &full[st]);
                     ++issued;
@@ -707,7 +789,9 @@ __global__ void __launch_bounds__(THREADS, 1)
     } else if (warp == EPI_WARPS + 1) {
         // ---------------- MMA issuer ----------------
         if (lane == 0) {
-            const uint32_t idesc = (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(BN >> 3) << 17) |
+            // D format F32 (1); A and B both BF16 (1) under kind::f16, both TF32 (2) under kind::tf32
+            constexpr uint32_t fmt = MODE == 2 ? 2u : 1u;
+            const uint32_t idesc = (1u << 4) | (fmt << 7) | (fmt << 10) | ((uint32_t)(BN >> 3) << 17) |
                                    ((uint32_t)(BM >> 4) << 24);
             int it = 0, cc = 0;  // k-blocks and accumulator chunks issued so far, over all tiles
             bool ok = true;
@@ -715,8 +799,8 @@ __global__ void __launch_bounds__(THREADS, 1)
             for (int i = 0; i < nkb; ++i, ++it) {
                 const int st = it % g.stages;
                 const uint32_t ph = (uint32_t)(it / g.stages) & 1u;
-                const bool first = (i % CHUNK_KB) == 0;
-                const bool last = (i % CHUNK_KB) == CHUNK_KB - 1 || i == nkb - 1;
+                const bool first = MODE == 0 ? (i % CHUNK_KB) == 0 : i == 0;
+                const bool last = MODE == 0 ? ((i % CHUNK_KB) == CHUNK_KB - 1 || i == nkb - 1) : i == nkb - 1;
                 if (first && cc > 0 && !mbar_wait(acc_empty, (uint32_t)(cc - 1) & 1u, g.err, g.wait_limit)) {
                     ok = false;
                     break;
@@ -728,6 +812,21 @@ __global__ void __launch_bounds__(THREADS, 1)
                 tc_fence_after();
                 const uint32_t sa = base + (uint32_t)st * g.stage_bytes;
                 const uint32_t sb = sa + g.a_bytes;
+                if (MODE != 0) {
+                    // two 32-byte K halves (16 BF16 or 8 TF32 each); every level
+                    // <= s-1 into the one FP32 accumulator
+                    for (int h = 0; h < 2; ++h) {
+                        bool f1 = first && h == 0;
+                        for (int L = 0; L < g.s; ++L)
+                            for (int t = 0; t <= L; ++t) {
+                                const uint64_t ad = sw64_desc(sa + t * (BM * 64) + h * 32);
+                                const uint64_t bd = sw64_desc(sb + (L - t) * (BN * 64) + h * 32);
+                                if (MODE == 2) tc_mma_tf32(tmem, ad, bd, idesc, f1 ? 0u : 1u);
+                                else tc_mma(tmem, ad, bd, idesc, f1 ? 0u : 1u);
+                                f1 = false;
+                            }
+                    }
+                } else
                 for (int h = 0; h < 2; ++h) {  // two K=16 halves, 32 bytes apart in the 64-byte row
                     const uint32_t restart = (first && h == 0) ? 0u : 1u;
                     tc_mma(tmem, sw64_desc(sa + h * 32), sw64_desc(sb + h * 32), idesc, restart);
@@ -751,6 +850,55 @@ __global__ void __launch_bounds__(THREADS, 1)
             tc_commit(drain);
             const long long t0 = clock64();
             while (!mbar_try_wait(drain, 0u) && clock64() - t0 < g.wait_limit) {
+            }
+        }
+    } else if (MODE != 0) {
+        // ---------------- epilogue of the FP32-accumulated modes ----------------
+        const int q = warp & 3, grp = warp >> 2;
+        const uint32_t lane_addr = tmem + ((uint32_t)(q * 32) << 16);
+        const bool unit_alpha = g.alpha == 1.0, zero_beta = g.beta == 0.0;
+        constexpr int dbits = MODE == 2 ? 11 : 8;  // digit width of the slices
+        int cc = 0;
+        for (int t = t_first; t < ntiles; t += t_step, ++cc) {
+            const int m0 = tile_m0(t), n0 = tile_n0(t);
+            const int m = m0 + q * 32 + lane;
+            const int ea = m < g.M ? g.eA[m] : 0;
+            if (!mbar_wait(acc_full, (uint32_t)cc & 1u, g.err, g.wait_limit)) break;
+            tc_fence_after();
+            float F[NBG][16];
+#pragma unroll
+            for (int jb = 0; jb < NBG; ++jb) {
+                const int b = grp + 3 * jb;
+                if (b >= NB16) continue;
+                uint32_t r[16];
+                tc_ld16(lane_addr + b * 16, r);
+                tc_wait_ld();
+#pragma unroll
+                for (int j = 0; j < 16; ++j) F[jb][j] = __uint_as_float(r[j]);
+            }
+            tc_fence_before();
+            __syncwarp();
+            if (lane == 0) mbar_arrive(acc_empty);
+#pragma unroll
+            for (int jb = 0; jb < NBG; ++jb) {
+                const int b = grp + 3 * jb;
+                if (b >= NB16) continue;
+                const int nl = n0 + b * 16 + (lane & 15);
+                const long long coff_l = nl < g.N ? view_offset32(g.out_c, (unsigned)nl) : 0;
+                const int eb_l = nl < g.N ? g.eB[nl] : 0;
+                double* crow = g.C + (m < g.M ? view_offset32(g.out_r, (unsigned)m) : 0);
+#pragma unroll
+                for (int j = 0; j < 16; ++j) {
+                    const long long coff = __shfl_sync(0xffffffffu, coff_l, j);
+                    const int eb = __shfl_sync(0xffffffffu, eb_l, j);
+                    const int n = n0 + b * 16 + j;
+                    if (m >= g.M || n >= g.N) continue;
+                    double v = f32_scaled(F[jb][j], ea + eb - 2 * dbits);
+                    if (ea > 1024 || eb > 1024) v = __longlong_as_double(0x7ff8000000000000ll);  // non-finite operand
+                    if (!unit_alpha) v *= g.alpha;
+                    double* cp = crow + coff;
+                    *cp = zero_beta ? v : fma(g.beta, *cp, v);
+                }
             }
         }
     } else {
@@ -892,6 +1040,7 @@ namespace {
 
 inline size_t align256(size_t b) { return (b + 255) & ~(size_t)255; }
 inline int k8_of(int K) { return (K + 7) & ~7; }
+inline int k4_of(int K) { return (K + 3) & ~3; }
 
 PFN_cuTensorMapEncodeTiled_v12000 tmap_encoder() {
     static PFN_cuTensorMapEncodeTiled_v12000 fn = nullptr;
@@ -907,16 +1056,19 @@ PFN_cuTensorMapEncodeTiled_v12000 tmap_encoder() {
     return fn;
 }
 
-// slices [s][R][K8] bf16, 64-byte-swizzled boxes of {32, rows, s}
-bool make_map(CUtensorMap* map, const void* slices, int R, int K8, int s, int box_rows) {
+// slices [s][R][Kp], 64-byte-swizzled boxes of {64 bytes of k, rows, s}:
+// BF16 (Kp = K8, 32 k per box row) or TF32 as FP32 (Kp = K4, 16 k)
+bool make_map(CUtensorMap* map, const void* slices, int R, int Kp, int s, int box_rows, bool tf32 = false) {
     auto enc = tmap_encoder();
     if (!enc) return false;
-    const cuuint64_t dims[3] = {(cuuint64_t)K8, (cuuint64_t)R, (cuuint64_t)s};
-    const cuuint64_t strides[2] = {(cuuint64_t)K8 * 2, (cuuint64_t)R * K8 * 2};
-    const cuuint32_t box[3] = {(cuuint32_t)oz::BK, (cuuint32_t)box_rows, (cuuint32_t)s};
+    const int esz = tf32 ? 4 : 2;
+    const cuuint64_t dims[3] = {(cuuint64_t)Kp, (cuuint64_t)R, (cuuint64_t)s};
+    const cuuint64_t strides[2] = {(cuuint64_t)Kp * esz, (cuuint64_t)R * Kp * esz};
+    const cuuint32_t box[3] = {(cuuint32_t)(64 / esz), (cuuint32_t)box_rows, (cuuint32_t)s};
     const cuuint32_t estr[3] = {1, 1, 1};
-    return enc(map, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 3, const_cast<void*>(slices), dims, strides, box, estr,
-               CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_64B, CU_TENSOR_MAP_L2_PROMOTION_L2_128B,
+    return enc(map, tf32 ? CU_TENSOR_MAP_DATA_TYPE_FLOAT32 : CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 3,
+               const_cast<void*>(slices), dims, strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE,
+               CU_TENSOR_MAP_SWIZZLE_64B, CU_TENSOR_MAP_L2_PROMOTION_L2_128B,
                CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
 }
 
@@ -926,7 +1078,9 @@ struct Plan {
     size_t smem, ws_bytes;
 };
 
-Plan plan_of(int M, int N, int K, int s) {
+// mode 2 (3xTF32) holds 16 k per 64-byte stage row instead of 32; modes 1 and
+// 2 never split K
+Plan plan_of(int M, int N, int K, int s, int mode = 0) {
     Plan p{};
     // fewest 144-wide tiles, then the narrowest 16-multiple width that covers N
     const int nt = (N + 143) / 144;
@@ -935,17 +1089,17 @@ Plan plan_of(int M, int N, int K, int s) {
     p.bn = 16 * p.nb16;
     p.m_tiles = (M + oz::BM - 1) / oz::BM;
     p.n_tiles = (N + p.bn - 1) / p.bn;
-    p.nkb = (k8_of(K) + oz::BK - 1) / oz::BK;
+    p.nkb = mode == 2 ? (k4_of(K) + 15) / 16 : (k8_of(K) + oz::BK - 1) / oz::BK;
     if (p.nkb < 1) p.nkb = 1;
     const int nchunks = (p.nkb + oz::CHUNK_KB - 1) / oz::CHUNK_KB;
     const int tiles = p.m_tiles * p.n_tiles;
     int ks = 1;
-    if (tiles < 120 && nchunks >= 2) ks = std::min(nchunks, (148 + tiles - 1) / tiles);
+    if (mode == 0 && tiles < 120 && nchunks >= 2) ks = std::min(nchunks, (148 + tiles - 1) / tiles);
     // int32 level sums stay exact for K <= 16384 per split
     const int max_chunks_per_split = 16384 / (oz::CHUNK_KB * oz::BK);
-    ks = std::max(ks, (nchunks + max_chunks_per_split - 1) / max_chunks_per_split);
+    if (mode == 0) ks = std::max(ks, (nchunks + max_chunks_per_split - 1) / max_chunks_per_split);
     const int cps = (nchunks + ks - 1) / ks;
-    p.kb_per_split = cps * oz::CHUNK_KB;
+    p.kb_per_split = mode == 0 ? cps * oz::CHUNK_KB : p.nkb;
     p.ksplit = (p.nkb + p.kb_per_split - 1) / p.kb_per_split;
     p.a_bytes = (uint32_t)(s * oz::BM * oz::BK * 2);
     p.stage_bytes = p.a_bytes + (uint32_t)(s * p.bn * oz::BK * 2);
@@ -955,7 +1109,7 @@ Plan plan_of(int M, int N, int K, int s) {
     return p;
 }
 
-template <int NB16, bool ONE>
+template <int NB16, bool ONE, int MODE = 0>
 cudaError_t launch_gemm(const Plan& p, const CUtensorMap& ta, const CUtensorMap& tb, const oz::GemmArgs& g,
                         cudaStream_t st) {
     // the 227 KB dynamic shared-memory opt-in is a per-device function
@@ -969,7 +1123,7 @@ cudaError_t launch_gemm(const Plan& p, const CUtensorMap& ta, const CUtensorMap&
     {
         std::lock_guard<std::mutex> lock(mu);
         if (!(done >> dev & 1ull)) {
-            e = cudaFuncSetAttribute(oz::k_oz_gemm<NB16, ONE>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+            e = cudaFuncSetAttribute(oz::k_oz_gemm<NB16, ONE, MODE>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                      227 * 1024);
             if (e != cudaSuccess) return e;
             done |= 1ull << dev;
@@ -985,7 +1139,7 @@ cudaError_t launch_gemm(const Plan& p, const CUtensorMap& ta, const CUtensorMap&
         grid = dim3((unsigned)std::min<long long>(tiles, nsm > 0 ? nsm : 1), 1, 1);
     }
     ++g_launches;
-    oz::k_oz_gemm<NB16, ONE><<<grid, oz::THREADS, p.smem, st>>>(ta, tb, g);
+    oz::k_oz_gemm<NB16, ONE, MODE><<<grid, oz::THREADS, p.smem, st>>>(ta, tb, g);
     return cudaGetLastError();
 }
 
@@ -997,6 +1151,43 @@ size_t oz_split_bytes(int R, int K, int s) {
 }
 inline const int* split_exponents(const void* buf, int R, int K8, int s) {
     return (const int*)((const char*)buf + align256((size_t)s * R * K8 * 2) + align256((size_t)R * 8));
+}
+// TF32 split buffer: slices [2][R][K4] (FP32) | row max bits [R] | exponents [R]
+size_t oz_split_tf32_bytes(int R, int K) {
+    return align256((size_t)2 * R * k4_of(K) * 4) + align256((size_t)R * 8) + align256((size_t)R * 4);
+}
+inline const int* split_tf32_exponents(const void* buf, int R, int K4) {
+    return (const int*)((const char*)buf + align256((size_t)2 * R * K4 * 4) + align256((size_t)R * 8));
+}
+
+cudaError_t oz_split_tf32(const double* X, int R, int K, const OzView& rvh, const OzView& kvh, void* buf,
+                          cudaStream_t st) {
+    if (R <= 0 || K <= 0 || rvh.n < 1 || rvh.n > 4 || kvh.n < 1 || kvh.n > 4) return cudaErrorInvalidValue;
+    oz::View rv, kv;
+    rv.n = rvh.n;
+    kv.n = kvh.n;
+    for (int a = 0; a < 4; ++a) {
+        rv.dim[a] = rvh.dim[a];
+        rv.stride[a] = rvh.stride[a];
+        kv.dim[a] = kvh.dim[a];
+        kv.stride[a] = kvh.stride[a];
+    }
+    const int K4 = k4_of(K);
+    float* sl = (float*)buf;
+    unsigned long long* mb = (unsigned long long*)((char*)buf + align256((size_t)2 * R * K4 * 4));
+    int* ex = const_cast<int*>(split_tf32_exponents(buf, R, K4));
+    cudaError_t e = cudaMemsetAsync(mb, 0, (size_t)R * 8, st);
+    if (e != cudaSuccess) return e;
+    const unsigned rg = (unsigned)((R + 31) / 32);
+    const unsigned kr = (unsigned)((K + oz::COLS_KRANGE - 1) / oz::COLS_KRANGE);
+    const unsigned long long warps = (unsigned long long)rg * kr;
+    const unsigned long long threads = (unsigned long long)R * (K4 / 4);
+    if ((warps + 3) / 4 > 0x7fffffffull || (threads + 255) / 256 > 0x7fffffffull) return cudaErrorInvalidValue;
+    ++g_launches;
+    oz::k_rowmax_cols<<<(unsigned)((warps + 3) / 4), 128, 0, st>>>(X, R, K, rv, kv, (int)kr, mb);
+    ++g_launches;
+    oz::k_split_tf32<<<(unsigned)((threads + 255) / 256), 256, 0, st>>>(X, R, K, K4, rv, kv, mb, sl, ex);
+    return cudaGetLastError();
 }
 
 template <int TPR>
@@ -1090,24 +1281,25 @@ cudaError_t wait_probe(long long limit_cycles, int arrive, int* err, cudaStream_
     return cudaGetLastError();
 }
 
-size_t oz_gemm_ws_bytes(int M, int N, int K, int s) { return plan_of(M, N, K, s).ws_bytes; }
+size_t oz_gemm_ws_bytes(int M, int N, int K, int s, int mode) { return plan_of(M, N, K, s, mode).ws_bytes; }
 
 cudaError_t oz_gemm(int M, int N, int K, int s, const void* Asplit, const void* Bsplit, double alpha, double beta,
-                    double* C, int ldc, void* ws, size_t ws_bytes, int* err, cudaStream_t st) {
+                    double* C, int ldc, void* ws, size_t ws_bytes, int* err, cudaStream_t st, int mode) {
     OzView r{1, {M, 1, 1, 1}, {ldc, 0, 0, 0}}, c{1, {N, 1, 1, 1}, {1, 0, 0, 0}};
-    return oz_gemm_view(M, N, K, s, Asplit, Bsplit, alpha, beta, C, r, c, ws, ws_bytes, err, st);
+    return oz_gemm_view(M, N, K, s, Asplit, Bsplit, alpha, beta, C, r, c, ws, ws_bytes, err, st, mode);
 }
 
 cudaError_t oz_gemm_view(int M, int N, int K, int s, const void* Asplit, const void* Bsplit, double alpha,
                          double beta, double* C, const OzView& orv, const OzView& ocv, void* ws, size_t ws_bytes,
-                         int* err, cudaStream_t st) {
+                         int* err, cudaStream_t st, int mode) {
     if (M <= 0 || N <= 0) return cudaSuccess;
-    if (K <= 0 || s < 2 || s > oz::MAX_S) return cudaErrorInvalidValue;
-    const Plan p = plan_of(M, N, K, s);
+    if (K <= 0 || s < 2 || s > oz::MAX_S || mode < 0 || mode > 2 || (mode == 2 && s != 2))
+        return cudaErrorInvalidValue;
+    const Plan p = plan_of(M, N, K, s, mode);
     if (p.stages < 2 || p.ws_bytes > ws_bytes) return cudaErrorInvalidValue;
-    const int K8 = k8_of(K);
+    const int Kp = mode == 2 ? k4_of(K) : k8_of(K);
     CUtensorMap ta, tb;
-    if (!make_map(&ta, Asplit, M, K8, s, oz::BM) || !make_map(&tb, Bsplit, N, K8, s, p.bn))
+    if (!make_map(&ta, Asplit, M, Kp, s, oz::BM, mode == 2) || !make_map(&tb, Bsplit, N, Kp, s, p.bn, mode == 2))
         return cudaErrorInvalidValue;
     oz::GemmArgs g{};
     g.M = M;
@@ -1118,8 +1310,8 @@ cudaError_t oz_gemm_view(int M, int N, int K, int s, const void* Asplit, const v
     g.stages = p.stages;
     g.a_bytes = p.a_bytes;
     g.stage_bytes = p.stage_bytes;
-    g.eA = split_exponents(Asplit, M, K8, s);
-    g.eB = split_exponents(Bsplit, N, K8, s);
+    g.eA = mode == 2 ? split_tf32_exponents(Asplit, M, Kp) : split_exponents(Asplit, M, Kp, s);
+    g.eB = mode == 2 ? split_tf32_exponents(Bsplit, N, Kp) : split_exponents(Bsplit, N, Kp, s);
     g.direct = p.ksplit == 1;
     g.alpha = alpha;
     g.beta = beta;
@@ -1147,6 +1339,29 @@ cudaError_t oz_gemm_view(int M, int N, int K, int s, const void* Asplit, const v
     // a CTA's K range: all of K (direct) or kb_per_split k-blocks (split-K)
     const bool one = (p.ksplit == 1 ? p.nkb : p.kb_per_split) <= oz::CHUNK_KB;
     cudaError_t e;
+    if (mode != 0) {
+        switch (p.nb16 * 4 + mode) {
+            case 5: e = launch_gemm<1, true, 1>(p, ta, tb, g, st); break;
+            case 6: e = launch_gemm<1, true, 2>(p, ta, tb, g, st); break;
+            case 9: e = launch_gemm<2, true, 1>(p, ta, tb, g, st); break;
+            case 10: e = launch_gemm<2, true, 2>(p, ta, tb, g, st); break;
+            case 13: e = launch_gemm<3, true, 1>(p, ta, tb, g, st); break;
+            case 14: e = launch_gemm<3, true, 2>(p, ta, tb, g, st); break;
+            case 17: e = launch_gemm<4, true, 1>(p, ta, tb, g, st); break;
+            case 18: e = launch_gemm<4, true, 2>(p, ta, tb, g, st); break;
+            case 21: e = launch_gemm<5, true, 1>(p, ta, tb, g, st); break;
+            case 22: e = launch_gemm<5, true, 2>(p, ta, tb, g, st); break;
+            case 25: e = launch_gemm<6, true, 1>(p, ta, tb, g, st); break;
+            case 26: e = launch_gemm<6, true, 2>(p, ta, tb, g, st); break;
+            case 29: e = launch_gemm<7, true, 1>(p, ta, tb, g, st); break;
+            case 30: e = launch_gemm<7, true, 2>(p, ta, tb, g, st); break;
+            case 33: e = launch_gemm<8, true, 1>(p, ta, tb, g, st); break;
+            case 34: e = launch_gemm<8, true, 2>(p, ta, tb, g, st); break;
+            case 37: e = launch_gemm<9, true, 1>(p, ta, tb, g, st); break;
+            default: e = launch_gemm<9, true, 2>(p, ta, tb, g, st); break;
+        }
+        return e;
+    }
     switch (p.nb16 * 2 + (one ? 1 : 0)) {
         case 2: e = launch_gemm<1, false>(p, ta, tb, g, st); break;
         case 3: e = launch_gemm<1, true>(p, ta, tb, g, st); break;

@@ -28,7 +28,7 @@ c_ip = ctypes.POINTER(ctypes.c_int)
 
 CTM_OK, CTM_NOT_CONVERGED = 0, 1
 CTM_ERR_ARG, CTM_ERR_OOM, CTM_ERR_CUDA, CTM_ERR_NONFINITE, CTM_ERR_TIMEOUT, CTM_ERR_STATE = -1, -2, -3, -4, -5, -6
-CTM_FP64, CTM_OZAKI_BF16 = 0, 1
+CTM_FP64, CTM_SPLIT_BF16, CTM_3XTF32, CTM_OZAKI_INT8, CTM_OZAKI_BF16 = 0, 1, 2, 3, 4
 ENV_INDEX = {"C1": 0, "T1": 1, "C2": 2, "T2": 3, "C3": 4, "T3": 5, "C4": 6, "T4": 7}
 
 
@@ -90,6 +90,9 @@ _sig("ctm_gemm_ozaki_workspace_bytes", c_size_t, c_int, c_int, c_int, c_int)
 _sig("ctm_gemm_ozaki", c_int, c_int, c_int, c_int, c_int, c_int, c_double, c_void_p, c_int, c_void_p, c_int,
      c_double, c_void_p, c_int, c_int, c_void_p, c_void_p)
 _sig("ctm_svd_noalloc", c_int, c_void_p, c_int, c_void_p, c_void_p, c_void_p, c_void_p)
+_sig("ctm_gemm_split_workspace_bytes", c_size_t, c_int, c_int, c_int, c_int)
+_sig("ctm_gemm_split", c_int, c_int, c_int, c_int, c_int, c_int, c_int, c_double, c_void_p, c_int, c_void_p, c_int,
+     c_double, c_void_p, c_int, c_void_p, c_void_p)
 _sig("ctm_log_norm_per_site", c_int, c_void_p, c_dp)
 _sig("ctm_init_env_random", c_int, c_void_p, ctypes.c_uint64)
 _sig("ctm_wait_probe", c_int, ctypes.c_longlong, c_int, c_void_p, c_void_p)
@@ -361,6 +364,15 @@ def ctm_gemm_ozaki_workspace_bytes(M, N, K, slices):
 def ctm_gemm_ozaki(transA, transB, M, N, K, alpha, A, lda, B, ldb, beta, C, ldc, slices, ws, stream=None):
     _check(_lib.ctm_gemm_ozaki(int(transA), int(transB), M, N, K, alpha, _dev_ptr(A), lda, _dev_ptr(B), ldb,
                                beta, _dev_ptr(C), ldc, slices, ctypes.c_void_p(ws.data_ptr()), _stream_ptr(stream)))
+
+
+def ctm_gemm_split_workspace_bytes(precision, M, N, K):
+    return _lib.ctm_gemm_split_workspace_bytes(precision, M, N, K)
+
+
+def ctm_gemm_split(precision, transA, transB, M, N, K, alpha, A, lda, B, ldb, beta, C, ldc, ws, stream=None):
+    _check(_lib.ctm_gemm_split(precision, int(transA), int(transB), M, N, K, alpha, _dev_ptr(A), lda, _dev_ptr(B),
+                               ldb, beta, _dev_ptr(C), ldc, ctypes.c_void_p(ws.data_ptr()), _stream_ptr(stream)))
 
 
 def ctm_svd_noalloc(G, k, U, S, V, stream=None):

@@ -94,3 +94,43 @@ def test_golden_emulated_fp64(ctm, name, sweeps):
     print(f"{name} emulated FP64 (5 slices): |dO| per observable vs the oracle {err}")
     assert err.max() <= 1e-8, err
     np.testing.assert_allclose(out["loop"], np.array(g["loop_spectra"]), atol=1e-8, rtol=0)
+
+
+def run_scheme(ctm, name, precision, slices, sweeps, tol, refine=0):
+    g, As, envs, d, D, chi, op1, op2 = case(name)
+    c = ctm.CTMRG(d, D, chi, precision=precision, ozaki_slices=slices, conv_measure=1, max_sweeps=sweeps,
+                  tol=tol, fp64_refine=refine)
+    c.set_tensors(As)
+    c.set_envs(envs)
+    st, n, delta = c.run()
+    obs = np.array([c.measure1(i, op1) for i in range(4)]
+                   + [c.measure2(i, dx, dy, op2) for (i, dx, dy) in I.SQUARE_2X2_BONDS])
+    loop = INV.loop_spectra(c.get_envs())
+    c.close()
+    return g, n, delta, obs, loop
+
+
+# (label, precision constant name, slices, bound on |dO| and on the loop
+# spectra).  Measured on a GB300 (max |dO|): split-BF16 9.2e-6, 3xTF32
+# 2.4e-5, emulated FP64 with 3 / 4 / 6 slices 1.4e-6 / 1.4e-8 / 4.0e-10; the
+# bounds leave a factor of 4 to 10.  The FP32-summed schemes stall at a loop-
+# moment change near 1e-5, the fixed point of FP32 rounding of sums over K up
+# to chi D^2.
+SCHEMES = [("split-BF16 (3 slices, FP32 sums)", "CTM_SPLIT_BF16", 3, 1e-4),
+           ("3xTF32 (FP32 sums)", "CTM_3XTF32", 2, 1e-4),
+           ("emulated FP64, 3 slices", "CTM_OZAKI_BF16", 3, 1e-5),
+           ("emulated FP64, 4 slices", "CTM_OZAKI_BF16", 4, 1e-7),
+           ("emulated FP64, 6 slices", "CTM_OZAKI_BF16", 6, 4e-9)]
+
+
+@pytest.mark.parametrize("label,pname,slices,bound", SCHEMES)
+def test_golden_precision_schemes(ctm, label, pname, slices, bound):
+    """Error of every observable of the precision workload (d=2, D=6,
+    chi=72) against the oracle, per contraction scheme, after up to 150
+    sweeps with the loop-moment stopping rule at 1e-10."""
+    g, n, delta, obs, loop = run_scheme(ctm, "neel_d2_D6_chi72", getattr(ctm, pname), slices, 150, 1e-10)
+    err = np.abs(obs - np.array(g["observables"]))
+    lerr = np.abs(loop - np.array(g["loop_spectra"])).max()
+    print(f"SCHEME {label}: {n} sweeps, loop-moment change {delta:.1e}, max |dO| {err.max():.2e} "
+          f"(site {err[:4].max():.2e}, bond {err[4:].max():.2e}), loop spectra {lerr:.2e}")
+    assert err.max() <= bound and lerr <= bound
