@@ -402,7 +402,50 @@ def case_sweep_chi64():
     c.close()
 
 
-CASES = {"apply_oz": case_apply_oz, "x3_oz": case_x3_oz, "qr": case_qr, "svd": case_svd,
+def case_peaks():
+    """Library dense-GEMM rates of the candidate slice types on this GPU
+    (cuBLAS through torch, 8192^3, CUDA events, 3 warm-ups, 10 timed) and
+    the FP64 DFMA rate of ctm_fp64_peak: the numbers that decide which
+    digit-slice types are worth a scheme."""
+    import torch
+    from paper_2112_13184_gb300 import ctm
+    n = 8192
+    out = {"fp64_dfma_tflops": ctm.ctm_fp64_peak()}
+
+    def rate(fn, flops):
+        for _ in range(3):
+            fn()
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        for _ in range(10):
+            fn()
+        e1.record()
+        torch.cuda.synchronize()
+        return flops * 10 / (e0.elapsed_time(e1) / 1e3) / 1e12
+
+    g = torch.Generator(device="cuda").manual_seed(0)
+    a = torch.randn(n, n, device="cuda", generator=g)
+    b = torch.randn(n, n, device="cuda", generator=g)
+    ab, bb = a.bfloat16(), b.bfloat16()
+    out["bf16_cublas_tflops"] = rate(lambda: ab @ bb, 2.0 * n ** 3)
+    torch.backends.cuda.matmul.allow_tf32 = True
+    out["tf32_cublas_tflops"] = rate(lambda: a @ b, 2.0 * n ** 3)
+    torch.backends.cuda.matmul.allow_tf32 = False
+    out["fp32_cublas_tflops"] = rate(lambda: a @ b, 2.0 * n ** 3)
+    ai = torch.randint(-127, 128, (n, n), device="cuda", dtype=torch.int8, generator=g)
+    bi = torch.randint(-127, 128, (n, n), device="cuda", dtype=torch.int8, generator=g)
+    try:
+        out["int8_cublas_tops"] = rate(lambda: torch._int_mm(ai, bi), 2.0 * n ** 3)
+    except RuntimeError as e:
+        out["int8_cublas_tops"] = None
+        out["int8_error"] = str(e).splitlines()[0]
+    ad, bd = a.double(), b.double()
+    out["fp64_cublas_tflops"] = rate(lambda: ad @ bd, 2.0 * n ** 3)
+    print(json.dumps({"case": "peaks", "n": n, **out}), flush=True)
+
+
+CASES = {"peaks": case_peaks, "apply_oz": case_apply_oz, "x3_oz": case_x3_oz, "qr": case_qr, "svd": case_svd,
          "sweep_chi64": case_sweep_chi64}
 
 

@@ -103,10 +103,12 @@ typedef struct {
                                corner spectra (ctm_spectrum_delta), 1 = the
                                gauge-invariant loop moments (ctm_loop_delta)   */
     int fp64_refine;        /* != 0 with a tensor-core mode: once ctm_run's measure
-                               falls below 1e-8 (about where the emulated
-                               products' rounding holds it) the handle switches
-                               to FP64 contractions for the remaining sweeps and
-                               stays in FP64 afterwards                          */
+                               falls below a decade above where the mode's
+                               rounding holds it (CTM_OZAKI_BF16: 1e-8 with 5+
+                               slices, 2e-7 with 4, 1e-5 with 3; CTM_SPLIT_BF16
+                               and CTM_3XTF32: 1e-4) the handle switches to FP64
+                               contractions for the remaining sweeps and stays
+                               in FP64 afterwards                               */
 } ctm_options;
 
 /* Defaults: chi=16, max_sweeps=100, tol=1e-10, FP64, 5 slices,

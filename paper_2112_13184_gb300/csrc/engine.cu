@@ -666,7 +666,18 @@ ctm_status one_sweep(ctm_ctx* h) {
 // Switches the handle's contractions between emulated FP64 and FP64 (every
 // buffer either needs exists from ctm_create on); the captured sweep graph
 // is dropped, the range finder's warm bases are kept.
-constexpr double FP64_REFINE_AT = 1e-8;
+// Where the loop-moment change of a scheme stalls (measured at d=2, D=6,
+// chi=72): FP32-summed split-BF16 / 3xTF32 near 1e-5, emulated FP64 with 3
+// slices near 1e-6, 4 slices near 2e-8, 5 and more below 1e-9.  fp64_refine
+// hands over to FP64 a decade above the stall.
+double refine_at(const ctm_options& o) {
+    switch (tc_mode_of(o.precision)) {
+        case 0: return o.ozaki_slices >= 5 ? 1e-8 : o.ozaki_slices == 4 ? 2e-7 : 1e-5;
+        case 1:
+        case 2: return 1e-4;
+        default: return 0.0;
+    }
+}
 ctm_status set_precision(ctm_ctx* h, int precision) {
     if (h->opt.precision == precision) return CTM_OK;
     if (precision != CTM_FP64 && precision != h->tc_prec) {
@@ -1233,9 +1244,9 @@ ctm_status ctm_run(ctm_handle h, int* sweeps_done, double* last_delta) {
         }
         prev.swap(cur);
         if (delta < h->opt.tol) { st = CTM_OK; break; }
-        if (h->opt.fp64_refine && tc_mode_of(h->opt.precision) >= 0 && delta < FP64_REFINE_AT) {
-            // the emulated products' rounding keeps the measure from falling
-            // much below this: the remaining sweeps run in FP64
+        if (h->opt.fp64_refine && tc_mode_of(h->opt.precision) >= 0 && delta < refine_at(h->opt)) {
+            // the tensor-core products' rounding keeps the measure from
+            // falling much below this: the remaining sweeps run in FP64
             CKS(set_precision(h, CTM_FP64));
         }
     }

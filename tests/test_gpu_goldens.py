@@ -134,3 +134,13 @@ def test_golden_precision_schemes(ctm, label, pname, slices, bound):
     print(f"SCHEME {label}: {n} sweeps, loop-moment change {delta:.1e}, max |dO| {err.max():.2e} "
           f"(site {err[:4].max():.2e}, bond {err[4:].max():.2e}), loop spectra {lerr:.2e}")
     assert err.max() <= bound and lerr <= bound
+
+
+def test_split_bf16_with_fp64_refine(ctm):
+    """split-BF16 until its loop-moment change falls below 1e-4, then FP64
+    to 1e-12: the observables reach the FP64 bar of the oracle."""
+    g, n, delta, obs, loop = run_scheme(ctm, "neel_d2_D6_chi72", ctm.CTM_SPLIT_BF16, 3, 150, 1e-12, refine=1)
+    err = np.abs(obs - np.array(g["observables"]))
+    print(f"split-BF16 + FP64 refinement: {n} sweeps, max |dO| {err.max():.2e}")
+    assert err.max() < 1e-9
+    np.testing.assert_allclose(loop, np.array(g["loop_spectra"]), atol=1e-9, rtol=0)
