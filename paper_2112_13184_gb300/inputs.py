@@ -126,6 +126,27 @@ def gauged_ising_tensors(beta: float, seed: int, strength: float = 0.5):
     return [np.ascontiguousarray(a) for a in As]
 
 
+def decoupled_chain_tensors(d: int, D: int, seed: int, axis: int = 0):
+    """Four sites whose legs across one axis carry only index 0, so that
+    every row (axis 0) or column (axis 1) of the lattice is an independent
+    infinite matrix-product state.  a_i ~ N(0, 1) (seed; sites in index
+    order), d x D x D [s, from, to]:
+      axis 0: A[s, l, 0, r, 0] = a_i[s, l, r]  (rows, tensors a_(0,y), a_(1,y))
+      axis 1: A[s, 0, u, 0, d] = a_i[s, d, u]  (columns, a_(x,0), a_(x,1))
+    zero elsewhere.  Returns (As, a)."""
+    rng = np.random.default_rng(seed)
+    a = [rng.standard_normal((d, D, D)) for _ in range(4)]
+    As = []
+    for t in a:
+        A = np.zeros((d, D, D, D, D))
+        if axis == 0:
+            A[:, :, 0, :, 0] = t
+        else:
+            A[:, 0, :, 0, :] = t.transpose(0, 2, 1)
+        As.append(A)
+    return As, a
+
+
 # --------------------------------------------------------------------------
 # environments
 # --------------------------------------------------------------------------
