@@ -339,6 +339,59 @@ ctm_status ctm_gemm_ozaki(int transA, int transB, int M, int N, int K, double al
                           const double* B, int ldb, double beta, double* C, int ldc, int slices, void* ws,
                           void* stream);
 
+/* ---- correlation functions and correlation length (Sec. 5.3) -------------
+ *
+ * Both read the handle's current environment (a converged one: run
+ * ctm_run or ctm_sweep first) and contract in the handle's precision; the
+ * eigenvalue and normalisation steps are FP64.  A strip is the row (for x)
+ * or column (for y) of sites through the start site, between the edge
+ * tensors of that row (T1 above, T3 below; for y T4 left, T2 right) and
+ * closed by the corner and edge tensors of its first and last sites. */
+#define CTM_CORRELATION_MAX_R 4096
+/* Correlation functions C(r, r0) = <A(r0) B(r0 + r)> (Sec. 5.3, the
+ * `correlation` section's definition): out_host[dir][site][i] for the
+ * displacement r = (i, 0) (dir 0) or (0, i) (dir 1), 0 <= i <= rmax, with
+ * every site r0 = (x, y), site = x + 2 y, of the cell as start site.  The
+ * strip with A on the ket of r0 and B on the ket of r0 + r divided by the
+ * same strip without operators; i = 0 is the one-site <A B> (B acts first).
+ * opA, opB: host d x d, row-major O[after, before].  out_host: 8 (rmax + 1)
+ * doubles.  rmax in [0, CTM_CORRELATION_MAX_R].  Cost: 3 rmax + 2 column
+ * contractions (each like one enlarged corner) per start site and
+ * direction.  Allocates 9 chi^2 D^2 + 4 d D^4 + 3 d^2 doubles on first use
+ * (kept until ctm_destroy) and 16 (rmax + 1) doubles per call.
+ * Synchronises.  CTM_ERR_STATE when tensors or environment are not set. */
+ctm_status ctm_correlation(ctm_handle h, const double* opA, const double* opB, int rmax, double* out_host);
+
+/* Leading eigenvalues of the transfer matrix of one period of the cell
+ * (Sec. 5.3, the `correlation_length` section: xi^-1 = e_1 =
+ * -log(lambda_1 / lambda_0), with e_2, e_3, ... for the finite-chi
+ * extrapolation 1/xi(inf) = 1/xi(chi) + k (e_2 - e_1)).  dir 0: the two
+ * columns of row y = index, acting along +x; dir 1: the two rows of column
+ * x = index, acting along +y.  Block subspace iteration with `block`
+ * orthonormal vectors (nev <= block <= 32, block <= chi^2 D^2; block >= nev
+ * + 2 converges faster) and a Rayleigh-Ritz step per iteration, until the
+ * first nev ratios lambda_i / lambda_0 change by less than tol in one
+ * iteration or max_iter iterations are done (then CTM_NOT_CONVERGED).
+ * out_host: 4 nev doubles -- Re(lambda_i / lambda_0), Im(lambda_i /
+ * lambda_0), |lambda_i|, e_i = -ln|lambda_i / lambda_0| / 2 per lattice
+ * spacing (the period is 2 sites; +inf for lambda_i = 0) -- for i < nev
+ * with |lambda_i| descending; the correlation length is 1 / e_1.  *iters,
+ * *change (optional): iterations done and the last change.  Each iteration
+ * costs 2 block column contractions.  Allocates 4 block chi^2 D^2 doubles
+ * plus a QR workspace per call.  Synchronises. */
+ctm_status ctm_transfer_spectrum(ctm_handle h, int dir, int index, int nev, int block, int max_iter, double tol,
+                                 double* out_host, int* iters, double* change);
+
+/* Kernel-level: eigenvalues of a small real m x m matrix H (device, row
+ * stride ldh, 1 <= m <= 32) -- Householder Hessenberg reduction, then the
+ * complex QR algorithm with Wilkinson shifts and deflation, in one thread.
+ * out (device, 4 m doubles): Re(l_i / l_0), Im(l_i / l_0), |l_i|,
+ * -ln|l_i / l_0| / period, with |l_i| descending.  *status (device,
+ * optional): 0; 1 when the iteration cap (60 m QR steps) was hit; 2 when
+ * every eigenvalue is zero.  Not synchronised.  (The Rayleigh-Ritz step of
+ * ctm_transfer_spectrum; no counterpart in the paper.) */
+ctm_status ctm_small_eig(const double* H, int m, int ldh, double period, double* out, int* status, void* stream);
+
 /* C[M,N] = alpha op(A) op(B) + beta C like ctm_dgemm, as the FP32-accumulated
  * tensor-core products of `precision` = CTM_SPLIT_BF16 (3 BF16 slices) or
  * CTM_3XTF32 (2 TF32 slices).  Error ~ 2^-24 K max|row of op(A)| max|col of

@@ -124,6 +124,9 @@ struct ctm_ctx {
     int* flag = nullptr;
     double* dotws = nullptr;   // partial sums of ctm::dot
     double* scal = nullptr;    // scalar results
+    // correlation strips (allocated on first use): 9 vectors of chi D^2 chi
+    // doubles, 4 ket tensors with an operator applied, 3 d x d operators
+    double* cv = nullptr;
 };
 
 namespace {
@@ -258,6 +261,17 @@ ctm_status alloc(ctm_ctx* h, void** p, size_t bytes) {
 template <class Tp>
 ctm_status allocd(ctm_ctx* h, Tp** p, size_t n) {
     return alloc(h, (void**)p, n * sizeof(Tp));
+}
+// scratch owned by the caller (cudaFree), for calls that size it per call
+template <class Tp>
+ctm_status allocd_tmp(ctm_ctx* h, Tp** p, size_t n) {
+    if (cudaMalloc((void**)p, (n ? n : 1) * sizeof(Tp)) != cudaSuccess) {
+        cudaGetLastError();
+        *p = nullptr;
+        h->err = "out of device memory";
+        return CTM_ERR_OOM;
+    }
+    return CTM_OK;
 }
 
 // ----------------------------------------------------------------------------
@@ -953,6 +967,240 @@ ctm_status log_norm_per_site(ctm_ctx* h, double* out) {
     return CTM_OK;
 }
 
+// ----------------------------------------------------------------------------
+// correlation functions and the transfer-matrix spectrum (Sec. 5.3)
+//
+// Strips run along +x' of a frame: frame 0 along +x, frame 3 (the lattice
+// rotated clockwise, where the original bottom edge is the frame's left
+// edge) along +y.  In frame m the roles C1..T4 are played by env[Cw(m)],
+// env[Tw(m)], ..., env[Tw(m+3)] and the site tensor by A[i][m].  A strip
+// vector L[b, l, l', t] (chi x D x D x chi) holds the contracted part left of
+// a column: b the open chi index toward the next T3, (l, l') the ket and bra
+// legs toward the next site, t the open chi index toward the next T1.
+//   left edge      L0 = C4 T4 C1
+//   one column     L'[b', r, r', t'] = L[b, l, l', t] T1[t, u, u', t']
+//                     Aket[s, l, u, r, d] Abra[s, l', u', r', d'] T3[b', d, d', b]
+//   right edge     R[t, r, r', b] = C2 T2 C3, closed as sum L[b,r,r',t] R[t,r,r',b]
+// The column is corner_core with (T1, L) in the roles of (C1 T1, T4) --
+// E[(b,d,d'), (t',r,r')] -- followed by one product with T3.
+// ----------------------------------------------------------------------------
+void frame_pos(int m, int i, int* x, int* y) {
+    for (int p = 0; p < 4; ++p)
+        if (FM.site(m, p % 2, p / 2) == i) {
+            *x = p % 2;
+            *y = p / 2;
+            return;
+        }
+    *x = *y = 0;
+}
+
+struct CorrBufs {
+    double* v[9];      // strip vectors
+    double* ket[4];    // Alu layouts [l,u,t,r,d] with an operator on the ket
+    double* op[3];     // d x d operators
+};
+ctm_status corr_bufs(ctm_ctx* h, CorrBufs* b) {
+    const size_t T = (size_t)h->chi * h->N, A = (size_t)h->d * h->D * h->D * h->D * h->D;
+    const size_t dd = (size_t)h->d * h->d;
+    if (!h->cv) CKS(allocd(h, &h->cv, 9 * T + 4 * A + 3 * dd));
+    for (int j = 0; j < 9; ++j) b->v[j] = h->cv + j * T;
+    for (int j = 0; j < 4; ++j) b->ket[j] = h->cv + 9 * T + j * A;
+    for (int j = 0; j < 3; ++j) b->op[j] = h->cv + 9 * T + 4 * A + j * dd;
+    return CTM_OK;
+}
+
+// L0[b, l, l', t] = C4[b, n] T4[n, l, l', a] C1[a, t] of site i in frame m
+ctm_status strip_left(ctm_ctx* h, int m, int i, double* out, double* tmp) {
+    const int chi = h->chi, N = h->N;
+    double** e = h->env[i];
+    CKS(gemm(h, false, false, chi, N, chi, e[Cw(m + 3)], chi, e[Tw(m + 3)], N, tmp, N));
+    return gemm(h, false, false, N, chi, chi, tmp, chi, e[Cw(m)], chi, out, chi);
+}
+// R[t, r, r', b] = C2[t, e] T2[e, r, r', f] C3[f, b], stored as [b, r, r', t]
+ctm_status strip_right(ctm_ctx* h, int m, int i, double* out, double* tmp, double* tmp2) {
+    const int chi = h->chi, N = h->N, D = h->D;
+    double** e = h->env[i];
+    CKS(gemm(h, false, false, chi, N, chi, e[Cw(m + 1)], chi, e[Tw(m + 1)], N, tmp, N));
+    CKS(gemm(h, false, false, N, chi, chi, tmp, chi, e[Cw(m + 2)], chi, tmp2, chi));
+    return perm(h, tmp2, out, {chi, D, D, chi}, {3, 1, 2, 0});
+}
+// one column of site i in frame m: out = L (T1 Aket Abra T3); ket in Alu layout
+ctm_status strip_column(ctm_ctx* h, int m, int i, const double* L, const double* ket, double* out, double* t3p,
+                        double* tmp) {
+    const int chi = h->chi, N = h->N, D = h->D;
+    double** e = h->env[i];
+    CKS(corner_core(h, e[Tw(m)], L, h->A[i][m & 3], ket, h->E[0], false));
+    // T3[k, d, d', b] -> [k, b, d, d'];  out'[k, (t', r, r')] = T3p[k, (b,d,d')] E[(b,d,d'), (t',r,r')]
+    CKS(perm(h, e[Tw(m + 2)], t3p, {chi, D, D, chi}, {0, 3, 1, 2}));
+    CKS(gemm(h, false, false, chi, N, N, t3p, N, h->E[0], N, tmp, N));
+    return perm(h, tmp, out, {chi, chi, D, D}, {0, 2, 3, 1});
+}
+// ket of site i in frame m with O[t, s] applied, in the Alu layout [l,u,t,r,d]
+// (tmp: d D^4 doubles)
+ctm_status ket_with_op(ctm_ctx* h, int m, int i, const double* op, double* out, double* tmp) {
+    const int d = h->d, D = h->D, D4 = D * D * D * D;
+    CK(ctm::dgemm(false, false, d, D4, d, 1.0, op, d, h->A[i][m & 3], D4, 0.0, tmp, D4, h->stream, nullptr, 0));
+    return perm(h, tmp, out, {d, D, D, D, D}, {1, 2, 0, 3, 4});
+}
+// L /= max|L| and X /= max|L| (the same factor: the ratio of two strips is kept)
+ctm_status rescale_pair(ctm_ctx* h, double* L, double* X) {
+    const size_t n = (size_t)h->chi * h->N;
+    CK(cudaMemsetAsync(h->maxbits + 8, 0, sizeof(unsigned long long), h->stream));
+    CK(ctm::maxabs(L, n, h->maxbits + 8, h->stream));
+    CK(ctm::scale_by_max(X, n, h->maxbits + 8, h->flag, h->stream));
+    CK(ctm::scale_by_max(L, n, h->maxbits + 8, h->flag, h->stream));
+    return CTM_OK;
+}
+
+// C[dir][site][r]: numerators and denominators on the device, one copy back
+ctm_status correlation(ctm_ctx* h, const double* opA_h, const double* opB_h, int rmax, double* out) {
+    CKS(check_ready(h));
+    CorrBufs b;
+    CKS(corr_bufs(h, &b));
+    const int d = h->d;
+    const size_t n = (size_t)h->chi * h->N, nvals = (size_t)2 * 4 * (rmax + 1);
+    double* nd = nullptr;  // [dir][site][r][num, den]
+    CKS(allocd_tmp(h, &nd, 2 * nvals));
+    ctm_status st = CTM_OK;
+    auto body = [&]() -> ctm_status {
+        CK(cudaMemcpyAsync(b.op[0], opA_h, sizeof(double) * d * d, cudaMemcpyHostToDevice, h->stream));
+        CK(cudaMemcpyAsync(b.op[1], opB_h, sizeof(double) * d * d, cudaMemcpyHostToDevice, h->stream));
+        // A B (B acts first)
+        CK(ctm::dgemm(false, false, d, d, d, 1.0, b.op[0], d, b.op[1], d, 0.0, b.op[2], d, h->stream, nullptr, 0));
+        double *LA = b.v[0], *L1 = b.v[1], *XB = b.v[2], *X1 = b.v[3], *tmp = b.v[4], *tmp2 = b.v[5];
+        double *t3p = b.v[6], *R = b.v[7], *L0 = b.v[8];
+        for (int dir = 0; dir < 2; ++dir) {
+            const int m = dir == 0 ? 0 : 3;
+            for (int i0 = 0; i0 < 4; ++i0) {
+                int x0, y0;
+                frame_pos(m, i0, &x0, &y0);
+                double* res = nd + 2 * ((size_t)(dir * 4 + i0) * (rmax + 1));
+                // r = 0: <A B> at r0
+                CKS(strip_left(h, m, i0, L0, tmp));
+                CKS(strip_right(h, m, i0, R, tmp, tmp2));
+                CKS(ket_with_op(h, m, i0, b.op[2], b.ket[0], b.ket[3]));
+                CKS(strip_column(h, m, i0, L0, b.ket[0], XB, t3p, tmp));
+                CKS(strip_column(h, m, i0, L0, h->Alu[i0][m & 3], L1, t3p, tmp));
+                CK(ctm::dot(XB, R, n, res + 0, h->dotws, h->stream));
+                CK(ctm::dot(L1, R, n, res + 1, h->dotws, h->stream));
+                if (rmax == 0) continue;
+                CKS(ket_with_op(h, m, i0, b.op[0], b.ket[0], b.ket[3]));
+                CKS(strip_column(h, m, i0, L0, b.ket[0], LA, t3p, tmp));
+                CKS(rescale_pair(h, L1, LA));
+                for (int r = 1; r <= rmax; ++r) {
+                    const int s = FM.site(m, x0 + r, y0);
+                    CKS(strip_right(h, m, s, R, tmp, tmp2));
+                    CKS(ket_with_op(h, m, s, b.op[1], b.ket[1], b.ket[3]));
+                    CKS(strip_column(h, m, s, LA, b.ket[1], XB, t3p, tmp));
+                    CKS(strip_column(h, m, s, L1, h->Alu[s][m & 3], X1, t3p, tmp));
+                    CK(ctm::dot(XB, R, n, res + 2 * r, h->dotws, h->stream));
+                    CK(ctm::dot(X1, R, n, res + 2 * r + 1, h->dotws, h->stream));
+                    if (r == rmax) break;
+                    CKS(strip_column(h, m, s, LA, h->Alu[s][m & 3], XB, t3p, tmp));
+                    std::swap(LA, XB);
+                    std::swap(L1, X1);
+                    CKS(rescale_pair(h, L1, LA));
+                }
+            }
+        }
+        std::vector<double> hv(2 * nvals);
+        CK(cudaMemcpyAsync(hv.data(), nd, sizeof(double) * 2 * nvals, cudaMemcpyDeviceToHost, h->stream));
+        CK(cudaStreamSynchronize(h->stream));
+        CKS(read_flag(h));
+        for (size_t j = 0; j < nvals; ++j) out[j] = hv[2 * j] / hv[2 * j + 1];
+        return CTM_OK;
+    };
+    st = body();
+    cudaStreamSynchronize(h->stream);
+    cudaFree(nd);
+    return st;
+}
+
+// Leading eigenvalues of the period transfer matrix of row `index` of frame
+// m: block subspace iteration V <- orth(T V) with Rayleigh-Ritz on
+// H = V (T V)^T; V holds `blk` orthonormal vectors as rows (blk x n).
+ctm_status transfer_spectrum(ctm_ctx* h, int dir, int index, int nev, int blk, int max_iter, double tol,
+                             double* out, int* iters, double* change) {
+    CKS(check_ready(h));
+    CorrBufs b;
+    CKS(corr_bufs(h, &b));
+    const int m = dir == 0 ? 0 : 3;
+    int xs, ys;
+    frame_pos(m, dir == 0 ? index * 2 : index, &xs, &ys);  // site (0, index) or (index, 0)
+    const int s0 = FM.site(m, 0, ys), s1 = FM.site(m, 1, ys);
+    const size_t n = (size_t)h->chi * h->N;
+    double *V = nullptr, *W = nullptr, *Y = nullptr, *Q = nullptr, *Rr = nullptr, *H = nullptr, *ev = nullptr;
+    void* qws = nullptr;
+    int* est = nullptr;
+    ctm_status st = CTM_OK;
+    auto body = [&]() -> ctm_status {
+        CKS(allocd_tmp(h, &V, (size_t)blk * n));
+        CKS(allocd_tmp(h, &W, (size_t)blk * n));
+        CKS(allocd_tmp(h, &Y, (size_t)blk * n));
+        CKS(allocd_tmp(h, &Q, (size_t)blk * n));
+        CKS(allocd_tmp(h, &Rr, (size_t)blk * blk));
+        CKS(allocd_tmp(h, &H, (size_t)blk * blk));
+        CKS(allocd_tmp(h, &ev, (size_t)4 * blk + 8));
+        if (cudaMalloc(&qws, ctm::qr_ws_bytes((int)n, blk)) != cudaSuccess) {
+            h->err = "transfer spectrum: out of device memory";
+            return CTM_ERR_OOM;
+        }
+        est = (int*)(ev + 4 * blk);
+        double *tmp = b.v[4], *t3p = b.v[6], *mid = b.v[7];
+        auto orth = [&](const double* src) -> ctm_status {  // V = rows of an orthonormal basis of src's rows
+            CKS(perm(h, src, Y, {blk, (int)n}, {1, 0}));
+            CK(ctm::qr(Y, (int)n, blk, Q, Rr, qws, h->stream, h->flag + 1));
+            return perm(h, Q, V, {(int)n, blk}, {1, 0});
+        };
+        CK(ctm::rng_normal(W, (size_t)blk * n, h->opt.seed, 0x5452414eull + h->rng_counter++, h->stream));
+        CKS(orth(W));
+        std::vector<double> prev(2 * nev, 0.0), cur(4 * blk);
+        double delta = INFINITY;
+        int it = 0;
+        st = CTM_NOT_CONVERGED;
+        for (it = 1; it <= max_iter; ++it) {
+            for (int j = 0; j < blk; ++j) {
+                CKS(strip_column(h, m, s0, V + (size_t)j * n, h->Alu[s0][m & 3], mid, t3p, tmp));
+                CKS(strip_column(h, m, s1, mid, h->Alu[s1][m & 3], W + (size_t)j * n, t3p, tmp));
+            }
+            // H[i][j] = v_i . (T v_j)
+            CK(ctm::dgemm(false, true, blk, blk, (int)n, 1.0, V, (int)n, W, (int)n, 0.0, H, blk, h->stream,
+                          h->splitk, h->splitk_n));
+            CK(ctm::small_eig(H, blk, blk, 2.0, ev, est, h->stream));
+            CK(cudaMemcpyAsync(cur.data(), ev, sizeof(double) * 4 * blk, cudaMemcpyDeviceToHost, h->stream));
+            CK(cudaStreamSynchronize(h->stream));
+            delta = 0.0;
+            for (int i = 0; i < nev; ++i) {
+                delta = std::max(delta, std::fabs(cur[i] - prev[2 * i]));
+                delta = std::max(delta, std::fabs(cur[blk + i] - prev[2 * i + 1]));
+                prev[2 * i] = cur[i];
+                prev[2 * i + 1] = cur[blk + i];
+            }
+            if (!(delta == delta)) delta = INFINITY;
+            CKS(orth(W));
+            if (delta < tol) {
+                st = CTM_OK;
+                break;
+            }
+        }
+        CKS(read_flag(h));
+        if (iters) *iters = std::min(it, max_iter);
+        if (change) *change = delta;
+        for (int i = 0; i < nev; ++i) {
+            out[i] = cur[i];
+            out[nev + i] = cur[blk + i];
+            out[2 * nev + i] = cur[2 * blk + i];
+            out[3 * nev + i] = cur[3 * blk + i];
+        }
+        return st;
+    };
+    st = body();
+    cudaStreamSynchronize(h->stream);
+    for (double* p : {V, W, Y, Q, Rr, H, ev}) cudaFree(p);
+    cudaFree(qws);
+    return st;
+}
+
 thread_local std::string g_err;
 
 }  // namespace
@@ -1473,6 +1721,31 @@ ctm_status ctm_gemm_split(int precision, int transA, int transB, int M, int N, i
                          st, mode);
     if (e != cudaSuccess) {
         g_err = std::string("ctm_gemm_split: ") + cudaGetErrorString(e);
+        return CTM_ERR_CUDA;
+    }
+    return CTM_OK;
+}
+
+ctm_status ctm_correlation(ctm_handle h, const double* opA, const double* opB, int rmax, double* out_host) {
+    if (!h || !opA || !opB || !out_host || rmax < 0 || rmax > CTM_CORRELATION_MAX_R) return CTM_ERR_ARG;
+    return correlation(h, opA, opB, rmax, out_host);
+}
+
+ctm_status ctm_transfer_spectrum(ctm_handle h, int dir, int index, int nev, int block, int max_iter, double tol,
+                                 double* out_host, int* iters, double* change) {
+    if (!h || !out_host || (dir != 0 && dir != 1) || index < 0 || index > 1 || nev < 1 || max_iter < 1 ||
+        !(tol >= 0.0))
+        return CTM_ERR_ARG;
+    const long long n = (long long)h->chi * h->N;
+    if (block < nev || block > ctm::small_eig_max() || block > n) return CTM_ERR_ARG;
+    return transfer_spectrum(h, dir, index, nev, block, max_iter, tol, out_host, iters, change);
+}
+
+ctm_status ctm_small_eig(const double* H, int m, int ldh, double period, double* out, int* status, void* stream) {
+    if (!H || !out || m < 1 || m > ctm::small_eig_max() || ldh < m || !(period > 0.0)) return CTM_ERR_ARG;
+    const cudaError_t e = ctm::small_eig(H, m, ldh, period, out, status, (cudaStream_t)stream);
+    if (e != cudaSuccess) {
+        g_err = std::string("ctm_small_eig: ") + cudaGetErrorString(e);
         return CTM_ERR_CUDA;
     }
     return CTM_OK;

@@ -60,6 +60,12 @@ cudaError_t svd(const double* G, int k, double* U, double* S, double* V, void* w
 // svd() with its workspace in a static device array (k <= svd_noalloc_max_k())
 int svd_noalloc_max_k();
 cudaError_t svd_noalloc(const double* G, int k, double* U, double* S, double* V, cudaStream_t s);
+// eigenvalues of a small real m x m matrix (m <= small_eig_max(), row stride
+// ldh): out[4m] = Re(l_i / l_0), Im(l_i / l_0), |l_i|, -ln|l_i / l_0| / period,
+// sorted by |l_i| descending; *status (optional) 0, 1 = QR iteration cap hit,
+// 2 = all eigenvalues zero
+int small_eig_max();
+cudaError_t small_eig(const double* H, int m, int ldh, double period, double* out, int* status, cudaStream_t s);
 // singular values only (descending) of a batch of nb k x k matrices, each
 // normalised to sum 1; Gs contiguous, out nb*k
 size_t svals_ws_bytes(int k, int nb);

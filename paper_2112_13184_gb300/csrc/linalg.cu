@@ -866,6 +866,203 @@ cudaError_t svd(const double* G, int k, double* U, double* S, double* V, void* w
     return cudaGetLastError();
 }
 
+// ---------------------------------------------------------------------------
+// Eigenvalues of a small real m x m matrix (m <= SMALL_EIG_MAX): reduction to
+// upper Hessenberg form by Householder reflections, then the QR algorithm in
+// complex arithmetic with one Wilkinson shift per step (the eigenvalue of
+// the trailing 2 x 2 block nearer its last diagonal entry; an exceptional
+// shift after 10 and 20 steps without deflation) and deflation where a
+// subdiagonal entry falls below 2^-52 of its two diagonal neighbours.  Only
+// the active diagonal block is updated: the eigenvalues of a block upper
+// triangular matrix are those of its diagonal blocks.  One thread; the
+// matrix lives in shared memory.
+// ---------------------------------------------------------------------------
+namespace {
+struct cd {
+    double re, im;
+};
+__device__ __forceinline__ cd c_mk(double r, double i) { return cd{r, i}; }
+__device__ __forceinline__ cd c_add(cd a, cd b) { return c_mk(a.re + b.re, a.im + b.im); }
+__device__ __forceinline__ cd c_sub(cd a, cd b) { return c_mk(a.re - b.re, a.im - b.im); }
+__device__ __forceinline__ cd c_mul(cd a, cd b) { return c_mk(a.re * b.re - a.im * b.im, a.re * b.im + a.im * b.re); }
+__device__ __forceinline__ cd c_conj(cd a) { return c_mk(a.re, -a.im); }
+__device__ __forceinline__ cd c_scale(cd a, double t) { return c_mk(a.re * t, a.im * t); }
+__device__ __forceinline__ double c_abs(cd a) { return hypot(a.re, a.im); }
+__device__ __forceinline__ double c_l1(cd a) { return fabs(a.re) + fabs(a.im); }
+// a / b by Smith's scaling, which avoids overflow in |b|^2
+__device__ __forceinline__ cd c_div(cd a, cd b) {
+    if (fabs(b.re) >= fabs(b.im)) {
+        const double r = b.im / b.re, den = b.re + b.im * r;
+        return c_mk((a.re + a.im * r) / den, (a.im - a.re * r) / den);
+    }
+    const double r = b.re / b.im, den = b.im + b.re * r;
+    return c_mk((a.re * r + a.im) / den, (a.im * r - a.re) / den);
+}
+// principal square root
+__device__ __forceinline__ cd c_sqrt(cd z) {
+    const double r = c_abs(z);
+    if (r == 0.0) return c_mk(0.0, 0.0);
+    const double t = sqrt(0.5 * (r + fabs(z.re)));
+    if (z.re >= 0.0) return c_mk(t, z.im / (2.0 * t));
+    return c_mk(fabs(z.im) / (2.0 * t), z.im >= 0.0 ? t : -t);
+}
+
+constexpr int SMALL_EIG_MAX = 32;
+
+__global__ void k_small_eig(const double* __restrict__ H, int m, int ldh, double period, double* __restrict__ out,
+                            int* __restrict__ status) {
+    __shared__ double R[SMALL_EIG_MAX][SMALL_EIG_MAX];
+    __shared__ cd Z[SMALL_EIG_MAX][SMALL_EIG_MAX];
+    __shared__ cd ev[SMALL_EIG_MAX];
+    __shared__ double v[SMALL_EIG_MAX];
+    __shared__ double gc[SMALL_EIG_MAX];
+    __shared__ cd gs[SMALL_EIG_MAX];
+    if (threadIdx.x != 0 || blockIdx.x != 0) return;
+    double hn = 0.0;
+    for (int i = 0; i < m; ++i)
+        for (int j = 0; j < m; ++j) {
+            R[i][j] = H[(size_t)i * ldh + j];
+            hn = fmax(hn, fabs(R[i][j]));
+        }
+    // Householder: R <- P R P with P = I - 2 v v^T / |v|^2 zeroing column k below k+1
+    for (int k = 0; k + 2 < m; ++k) {
+        double a2 = 0.0;
+        for (int i = k + 1; i < m; ++i) a2 += R[i][k] * R[i][k];
+        if (a2 == 0.0) continue;
+        const double alpha = R[k + 1][k] > 0.0 ? -sqrt(a2) : sqrt(a2);
+        double vn2 = 0.0;
+        for (int i = k + 1; i < m; ++i) {
+            v[i] = R[i][k] - (i == k + 1 ? alpha : 0.0);
+            vn2 += v[i] * v[i];
+        }
+        if (vn2 == 0.0) continue;
+        for (int j = k; j < m; ++j) {
+            double t = 0.0;
+            for (int i = k + 1; i < m; ++i) t += v[i] * R[i][j];
+            t *= 2.0 / vn2;
+            for (int i = k + 1; i < m; ++i) R[i][j] -= t * v[i];
+        }
+        for (int i = 0; i < m; ++i) {
+            double t = 0.0;
+            for (int j = k + 1; j < m; ++j) t += R[i][j] * v[j];
+            t *= 2.0 / vn2;
+            for (int j = k + 1; j < m; ++j) R[i][j] -= t * v[j];
+        }
+        for (int i = k + 2; i < m; ++i) R[i][k] = 0.0;
+    }
+    for (int i = 0; i < m; ++i)
+        for (int j = 0; j < m; ++j) Z[i][j] = c_mk(R[i][j], 0.0);
+    const double eps = 0x1p-52;
+    const double tiny = hn > 0.0 ? eps * hn * 1e-30 : 1e-300;
+    int st = 0, hi = m - 1, its = 0, total = 0;
+    while (hi >= 0) {
+        if (hi == 0) {
+            ev[0] = Z[0][0];
+            break;
+        }
+        int l = hi;
+        for (; l > 0; --l) {
+            const double sc = c_l1(Z[l - 1][l - 1]) + c_l1(Z[l][l]);
+            if (c_l1(Z[l][l - 1]) <= eps * sc || c_l1(Z[l][l - 1]) <= tiny) {
+                Z[l][l - 1] = c_mk(0.0, 0.0);
+                break;
+            }
+        }
+        if (l == hi) {
+            ev[hi] = Z[hi][hi];
+            --hi;
+            its = 0;
+            continue;
+        }
+        if (++total > 60 * m) {
+            st = 1;  // not converged: report the current diagonal
+            for (int i = 0; i <= hi; ++i) ev[i] = Z[i][i];
+            break;
+        }
+        cd shift;
+        if (its == 10 || its == 20) {
+            shift = c_add(Z[hi][hi], c_mk(0.75 * c_abs(Z[hi][hi - 1]), 0.0));
+        } else {
+            const cd a = Z[hi - 1][hi - 1], b = Z[hi - 1][hi], c = Z[hi][hi - 1], d = Z[hi][hi];
+            const cd half = c_scale(c_add(a, d), 0.5), dif = c_scale(c_sub(a, d), 0.5);
+            const cd disc = c_sqrt(c_add(c_mul(dif, dif), c_mul(b, c)));
+            const cd mu1 = c_add(half, disc), mu2 = c_sub(half, disc);
+            shift = c_abs(c_sub(mu1, d)) <= c_abs(c_sub(mu2, d)) ? mu1 : mu2;
+        }
+        ++its;
+        for (int i = l; i <= hi; ++i) Z[i][i] = c_sub(Z[i][i], shift);
+        // Z - shift = Q R by Givens rotations G_k on rows k, k+1 ...
+        for (int k = l; k < hi; ++k) {
+            const cd f = Z[k][k], g = Z[k + 1][k];
+            const double fa = c_abs(f), ga = c_abs(g);
+            double c;
+            cd sn;
+            if (ga == 0.0) {
+                c = 1.0;
+                sn = c_mk(0.0, 0.0);
+            } else if (fa == 0.0) {
+                c = 0.0;
+                sn = c_scale(c_conj(g), 1.0 / ga);
+            } else {
+                const double r = hypot(fa, ga);
+                c = fa / r;
+                sn = c_scale(c_mul(c_scale(f, 1.0 / fa), c_conj(g)), 1.0 / r);
+            }
+            gc[k] = c;
+            gs[k] = sn;
+            for (int j = k; j <= hi; ++j) {
+                const cd x = Z[k][j], y = Z[k + 1][j];
+                Z[k][j] = c_add(c_scale(x, c), c_mul(sn, y));
+                Z[k + 1][j] = c_sub(c_scale(y, c), c_mul(c_conj(sn), x));
+            }
+        }
+        // ... then R Q: G_k^H on columns k, k+1
+        for (int k = l; k < hi; ++k) {
+            const double c = gc[k];
+            const cd sn = gs[k];
+            const int last = min(k + 2, hi);
+            for (int i = l; i <= last; ++i) {
+                const cd x = Z[i][k], y = Z[i][k + 1];
+                Z[i][k] = c_add(c_scale(x, c), c_mul(y, c_conj(sn)));
+                Z[i][k + 1] = c_sub(c_scale(y, c), c_mul(x, sn));
+            }
+        }
+        for (int i = l; i <= hi; ++i) Z[i][i] = c_add(Z[i][i], shift);
+    }
+    // descending modulus (stable insertion sort)
+    for (int i = 1; i < m; ++i) {
+        const cd x = ev[i];
+        const double ax = c_abs(x);
+        int j = i - 1;
+        while (j >= 0 && c_abs(ev[j]) < ax) {
+            ev[j + 1] = ev[j];
+            --j;
+        }
+        ev[j + 1] = x;
+    }
+    const double a0 = c_abs(ev[0]);
+    if (a0 == 0.0) st = st ? st : 2;
+    for (int i = 0; i < m; ++i) {
+        const double ai = c_abs(ev[i]);
+        const cd r = a0 > 0.0 ? c_div(ev[i], ev[0]) : c_mk(0.0, 0.0);
+        out[i] = r.re;
+        out[m + i] = r.im;
+        out[2 * m + i] = ai;
+        out[3 * m + i] = (a0 > 0.0 && ai > 0.0) ? -log(ai / a0) / period : INFINITY;
+    }
+    if (status) *status = st;
+}
+}  // namespace
+
+int small_eig_max() { return SMALL_EIG_MAX; }
+
+cudaError_t small_eig(const double* H, int m, int ldh, double period, double* out, int* status, cudaStream_t s) {
+    if (m < 1 || m > SMALL_EIG_MAX || ldh < m || !H || !out || !(period > 0.0)) return cudaErrorInvalidValue;
+    ++g_launches;
+    k_small_eig<<<1, 32, 0, s>>>(H, m, ldh, period, out, status);
+    return cudaGetLastError();
+}
+
 size_t svals_ws_bytes(int k, int nb) {
     return sizeof(double) * (size_t)nb * ((size_t)k * k + k) + sizeof(unsigned long long) * JACOBI_MAX_SWEEPS * nb +
            256;

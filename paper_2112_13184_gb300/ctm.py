@@ -90,6 +90,10 @@ _sig("ctm_gemm_ozaki_workspace_bytes", c_size_t, c_int, c_int, c_int, c_int)
 _sig("ctm_gemm_ozaki", c_int, c_int, c_int, c_int, c_int, c_int, c_double, c_void_p, c_int, c_void_p, c_int,
      c_double, c_void_p, c_int, c_int, c_void_p, c_void_p)
 _sig("ctm_svd_noalloc", c_int, c_void_p, c_int, c_void_p, c_void_p, c_void_p, c_void_p)
+_sig("ctm_correlation", c_int, c_void_p, c_void_p, c_void_p, c_int, c_void_p)
+_sig("ctm_transfer_spectrum", c_int, c_void_p, c_int, c_int, c_int, c_int, c_int, c_double, c_void_p,
+     ctypes.POINTER(c_int), ctypes.POINTER(c_double))
+_sig("ctm_small_eig", c_int, c_void_p, c_int, c_int, c_double, c_void_p, c_void_p, c_void_p)
 _sig("ctm_gemm_split_workspace_bytes", c_size_t, c_int, c_int, c_int, c_int)
 _sig("ctm_gemm_split", c_int, c_int, c_int, c_int, c_int, c_int, c_int, c_double, c_void_p, c_int, c_void_p, c_int,
      c_double, c_void_p, c_int, c_void_p, c_void_p)
@@ -221,6 +225,33 @@ def ctm_log_norm_per_site(h):
     v = c_double()
     _check(_lib.ctm_log_norm_per_site(h, ctypes.byref(v)), h)
     return v.value
+
+
+def ctm_correlation(h, opA, opB, rmax):
+    """C[dir, site, r] = <A(r0) B(r0 + r e_dir)>, dir 0: x, 1: y."""
+    a, b = _host(opA), _host(opB)
+    out = np.zeros((2, 4, rmax + 1))
+    _check(_lib.ctm_correlation(h, _dp(a), _dp(b), rmax, _dp(out)), h)
+    return out
+
+
+def ctm_transfer_spectrum(h, direction, index, nev=4, block=None, max_iter=200, tol=1e-10):
+    """(ratio lambda_i / lambda_0 [complex, nev], |lambda_i| [nev], e_i [nev],
+    iterations, last change, status)."""
+    block = block if block is not None else nev + 4
+    out = np.zeros(4 * nev)
+    it, ch = c_int(), c_double()
+    st = _lib.ctm_transfer_spectrum(h, direction, index, nev, block, max_iter, tol, _dp(out), ctypes.byref(it),
+                                    ctypes.byref(ch))
+    if st not in (CTM_OK, CTM_NOT_CONVERGED):
+        _check(st, h)
+    ratio = out[:nev] + 1j * out[nev:2 * nev]
+    return ratio, out[2 * nev:3 * nev], out[3 * nev:], it.value, ch.value, st
+
+
+def ctm_small_eig(H, m, ldh, period, out, status, stream=None):
+    _check(_lib.ctm_small_eig(_dev_ptr(H), m, ldh, period, _dev_ptr(out), ctypes.c_void_p(status.data_ptr()),
+                              _stream_ptr(stream)))
 
 
 def ctm_init_env_random(h, seed):
@@ -456,6 +487,12 @@ class CTMRG:
 
     def log_norm_per_site(self):
         return ctm_log_norm_per_site(self.h)
+
+    def correlation(self, opA, opB, rmax):
+        return ctm_correlation(self.h, opA, opB, rmax)
+
+    def transfer_spectrum(self, direction, index, nev=4, block=None, max_iter=200, tol=1e-10):
+        return ctm_transfer_spectrum(self.h, direction, index, nev, block, max_iter, tol)
 
     def init_env_random(self, seed):
         ctm_init_env_random(self.h, seed)
