@@ -59,6 +59,7 @@ def parse():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-gate", action="store_true", help="skip the FP64 arm and the |dE| gate")
     ap.add_argument("--no-serve", action="store_true", help="skip the serving-latency leg")
+    ap.add_argument("--no-corr", action="store_true", help="skip the correlation-function leg")
     ap.add_argument("--case", default=None, choices=sorted(CASES), help="run one profiling case and exit")
     return ap.parse_args()
 
@@ -309,6 +310,27 @@ def gate_leg(C, w, mixed, stream, slices):
             "gate_dE_le_1e-8": bool(dE.max() <= 1e-8)}
 
 
+def correlation_leg(C, w, solver, rmax=8, nev=4, block=8, max_iter=40):
+    """Sec. 5.3 on the solver's current environment (the gate leaves it at
+    the mixed fixed point): <op1(r0) op1(r0 + r)> for r <= rmax along x and
+    y from all four sites, and the leading transfer-matrix eigenvalues of
+    row 0 along x.  Wall time of each call (both synchronise); a column
+    contraction is one enlarged-corner core plus one product with T3."""
+    t0 = time.perf_counter()
+    corr = solver.correlation(w["op1"], w["op1"], rmax)
+    t_corr = time.perf_counter() - t0
+    cols = 2 * 4 * (3 * rmax + 2)
+    t0 = time.perf_counter()
+    ratio, mod, e, it, ch, st = solver.transfer_spectrum(0, 0, nev=nev, block=block, max_iter=max_iter, tol=1e-10)
+    t_tm = time.perf_counter() - t0
+    return {"rmax": rmax, "seconds": t_corr, "column_contractions": cols, "ms_per_column": 1e3 * t_corr / cols,
+            "C_x_site0": [float(x) for x in corr[0, 0]], "C_y_site0": [float(x) for x in corr[1, 0]],
+            "transfer": {"seconds": t_tm, "iterations": it, "last_change": ch, "converged": st == C.CTM_OK,
+                         "block": block, "column_contractions": 2 * block * it,
+                         "abs_ratio": [float(x) for x in np.abs(ratio)], "e": [float(x) for x in e[1:]],
+                         "xi_lattice_spacings": float(1.0 / e[1]) if e[1] > 0 else None}}
+
+
 def serve_leg(seed=0):
     """Bounded serving-latency leg: a Poisson stream of 12 CTMRG+observable
     requests at 4 per second from the transverse-field-scan family (d in
@@ -529,6 +551,9 @@ def run_ours(args):
     gate = None
     if prec != C.CTM_FP64 and not args.no_gate and world == 1:
         gate = gate_leg(C, w, solver, stream, args.slices)
+    corr = None
+    if not args.no_corr and world == 1:
+        corr = correlation_leg(C, w, solver)
     latency = None
     if not args.no_serve and world == 1:
         latency = serve_leg()
@@ -564,6 +589,7 @@ def run_ours(args):
             "clocks": clk.summary(),
             "gate": gate,
             "latency": latency,
+            "correlation": corr,
             "fp64_peak_tflops": fp64_peak,
             "profile_note": prof_note,
             "profile_by_op": {k: {"ms": round(v["ms"], 3), "calls": v["calls"], "launches": v.get("launches")}

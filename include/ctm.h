@@ -129,6 +129,17 @@ ctm_status ctm_footprint_bytes(int d, int D, const ctm_options* opt, size_t* byt
  * handle.  Allocates all device memory up front (CTM_ERR_OOM if it does not
  * fit); *out is NULL on any error, with the message in ctm_last_error(NULL). */
 ctm_status ctm_create(int Lx, int Ly, int d, int D, const ctm_options* opt, void* stream, ctm_handle* out);
+/* ctm_create with every device buffer of the handle carved from a
+ * caller-owned arena: `arena` (device, 256-byte aligned) of arena_bytes >=
+ * ctm_footprint_bytes(d, D, opt) bytes.  The handle never calls cudaMalloc
+ * or cudaFree for them, so creating and destroying handles inside a running
+ * server neither allocates nor waits for other streams' work; the arena
+ * stays the caller's and must outlive the handle.  Per-call scratch of
+ * ctm_correlation / ctm_transfer_spectrum / ctm_log_norm_per_site is still
+ * allocated per call.  (No counterpart in the paper: the serving loop's
+ * memory pool.) */
+ctm_status ctm_create_in(int Lx, int Ly, int d, int D, const ctm_options* opt, void* stream, void* arena,
+                         size_t arena_bytes, ctm_handle* out);
 ctm_status ctm_destroy(ctm_handle h);
 
 /* Copy in the site tensor A of site i (d*D^4 doubles, C-order [s,l,u,r,d]). */

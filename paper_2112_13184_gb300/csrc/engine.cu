@@ -127,6 +127,10 @@ struct ctm_ctx {
     // correlation strips (allocated on first use): 9 vectors of chi D^2 chi
     // doubles, 4 ket tensors with an operator applied, 3 d x d operators
     double* cv = nullptr;
+    // caller-owned device arena (ctm_create_in): every buffer is carved from
+    // it and nothing is freed on destroy
+    char* arena = nullptr;
+    size_t arena_n = 0, arena_used = 0;
 };
 
 namespace {
@@ -238,6 +242,7 @@ size_t footprint(int d, int D, const ctm_options& o) {
     size_t bytes = dbl * sizeof(double);
     bytes += qr_ws_bytes(N, k) + svd_ws_bytes(k) + svals_ws_bytes(chi, 16);
     bytes += 64 * sizeof(unsigned long long) + 64 + 64 * 256;
+    bytes += 256 * 256;  // 256-byte alignment of up to 256 buffers carved from an arena
     bytes += sizeof(double) * (ctm::dot_ws_doubles() + 8);
     const int mode = tc_mode_of(o.precision);
     if (mode >= 0) {
@@ -249,6 +254,16 @@ size_t footprint(int d, int D, const ctm_options& o) {
 }
 
 ctm_status alloc(ctm_ctx* h, void** p, size_t bytes) {
+    if (h->arena) {
+        const size_t at = (h->arena_used + 255) & ~(size_t)255, need = bytes ? bytes : 8;
+        if (at > h->arena_n || need > h->arena_n - at) {
+            h->err = "device arena exhausted";
+            return CTM_ERR_OOM;
+        }
+        *p = h->arena + at;
+        h->arena_used = at + need;
+        return CTM_OK;
+    }
     cudaError_t e = cudaMalloc(p, bytes ? bytes : 8);
     if (e != cudaSuccess) {
         h->err = std::string("cudaMalloc: ") + cudaGetErrorString(e);
@@ -1261,7 +1276,31 @@ ctm_status ctm_footprint_bytes(int d, int D, const ctm_options* o, size_t* bytes
     return CTM_OK;
 }
 
+namespace {
+ctm_status create(int Lx, int Ly, int d, int D, const ctm_options* o, void* stream, void* arena, size_t arena_n,
+                  ctm_handle* out);
+}
+
 ctm_status ctm_create(int Lx, int Ly, int d, int D, const ctm_options* o, void* stream, ctm_handle* out) {
+    return create(Lx, Ly, d, D, o, stream, nullptr, 0, out);
+}
+
+ctm_status ctm_create_in(int Lx, int Ly, int d, int D, const ctm_options* o, void* stream, void* arena,
+                         size_t arena_bytes, ctm_handle* out) {
+    if (!arena || ((uintptr_t)arena & 255) != 0) {
+        g_err = "ctm_create_in: the arena must be a device pointer aligned to 256 bytes";
+        return CTM_ERR_ARG;
+    }
+    if (o && validate(d, D, o) == CTM_OK && arena_bytes < footprint(d, D, *o)) {
+        g_err = "ctm_create_in: the arena is smaller than ctm_footprint_bytes";
+        return CTM_ERR_ARG;
+    }
+    return create(Lx, Ly, d, D, o, stream, arena, arena_bytes, out);
+}
+
+namespace {
+ctm_status create(int Lx, int Ly, int d, int D, const ctm_options* o, void* stream, void* arena, size_t arena_n,
+                  ctm_handle* out) {
     if (!out) return CTM_ERR_ARG;
     *out = nullptr;
     if (Lx != 2 || Ly != 2) {
@@ -1278,6 +1317,8 @@ ctm_status ctm_create(int Lx, int Ly, int d, int D, const ctm_options* o, void* 
     }
     ctm_ctx* h = new (std::nothrow) ctm_ctx();
     if (!h) return CTM_ERR_OOM;
+    h->arena = (char*)arena;
+    h->arena_n = arena_n;
     h->d = d;
     h->D = D;
     h->opt = *o;
@@ -1358,6 +1399,7 @@ ctm_status ctm_create(int Lx, int Ly, int d, int D, const ctm_options* o, void* 
     *out = h;
     return CTM_OK;
 }
+}  // namespace
 
 ctm_status ctm_destroy(ctm_handle h) {
     if (!h) return CTM_OK;

@@ -90,6 +90,8 @@ _sig("ctm_gemm_ozaki_workspace_bytes", c_size_t, c_int, c_int, c_int, c_int)
 _sig("ctm_gemm_ozaki", c_int, c_int, c_int, c_int, c_int, c_int, c_double, c_void_p, c_int, c_void_p, c_int,
      c_double, c_void_p, c_int, c_int, c_void_p, c_void_p)
 _sig("ctm_svd_noalloc", c_int, c_void_p, c_int, c_void_p, c_void_p, c_void_p, c_void_p)
+_sig("ctm_create_in", c_int, c_int, c_int, c_int, c_int, ctypes.POINTER(ctm_options), c_void_p, c_void_p, c_size_t,
+     c_void_p)
 _sig("ctm_correlation", c_int, c_void_p, c_void_p, c_void_p, c_int, c_void_p)
 _sig("ctm_transfer_spectrum", c_int, c_void_p, c_int, c_int, c_int, c_int, c_int, c_double, c_void_p,
      ctypes.POINTER(c_int), ctypes.POINTER(c_double))
@@ -164,6 +166,14 @@ def ctm_footprint_bytes(d, D, opt: ctm_options) -> int:
 def ctm_create(d, D, opt: ctm_options, stream=None, Lx=2, Ly=2):
     h = c_void_p()
     _check(_lib.ctm_create(Lx, Ly, d, D, ctypes.byref(opt), _stream_ptr(stream), ctypes.byref(h)), None)
+    return h
+
+
+def ctm_create_in(d, D, opt: ctm_options, arena_ptr, arena_bytes, stream=None, Lx=2, Ly=2):
+    """ctm_create with every buffer carved from [arena_ptr, arena_ptr + arena_bytes)."""
+    h = c_void_p()
+    _check(_lib.ctm_create_in(Lx, Ly, d, D, ctypes.byref(opt), _stream_ptr(stream), ctypes.c_void_p(arena_ptr),
+                              c_size_t(arena_bytes), ctypes.byref(h)), None)
     return h
 
 
@@ -417,10 +427,16 @@ def ctm_svd_noalloc(G, k, U, S, V, stream=None):
 class CTMRG:
     """One 2x2-cell CTMRG instance on the current CUDA device."""
 
-    def __init__(self, d, D, chi, stream=None, **opts):
+    def __init__(self, d, D, chi, stream=None, arena=None, **opts):
+        """arena: optional (device pointer, bytes) the handle's buffers are
+        carved from (ctm_create_in)."""
         self.d, self.D, self.chi = d, D, chi
+        self.stream = stream
         self.opt = ctm_default_options(chi=chi, **opts)
-        self.h = ctm_create(d, D, self.opt, stream)
+        if arena is None:
+            self.h = ctm_create(d, D, self.opt, stream)
+        else:
+            self.h = ctm_create_in(d, D, self.opt, arena[0], arena[1], stream)
 
     def close(self):
         if self.h:

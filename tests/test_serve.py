@@ -12,26 +12,41 @@ from paper_2112_13184_gb300.serve import Request, Server
 
 
 class FakeBackend:
-    """Handles that 'converge' after a set number of sweeps; records order."""
+    """Handles that 'converge' after a set number of sweeps; a launched
+    sweep of request rid completes after lag[rid] polls (0: at once);
+    records order."""
 
-    def __init__(self, bytes_of, sweeps_to_converge):
+    def __init__(self, bytes_of, sweeps_to_converge, lag=None, floor=None):
         self.bytes_of = bytes_of
         self.need = sweeps_to_converge
-        self.opened, self.closed, self.live, self.peak = [], [], 0, 0
+        self.lag = lag or {}
+        self.floor = floor or {}
+        self.opened, self.closed, self.live, self.peak, self.refined = [], [], 0, 0, []
+        self.launches = []
 
     def footprint(self, r):
         return self.bytes_of[r.rid]
 
-    def open(self, r):
+    def open(self, r, block=None):
         self.opened.append(r.rid)
         self.live += self.bytes_of[r.rid]
         self.peak = max(self.peak, self.live)
-        return {"rid": r.rid, "n": 0}
+        return {"rid": r.rid, "n": 0, "wait": 0, "refined": False}
 
-    def sweep_async(self, h):
-        h["n"] += 1
+    def launch(self, h, n):
+        h["n"] += n
+        h["wait"] = self.lag.get(h["rid"], 0)
+        self.launches.append(h["rid"])
+
+    def ready(self, h):
+        if h["wait"] > 0:
+            h["wait"] -= 1
+            return False
+        return True
 
     def delta(self, h):
+        if h["rid"] in self.floor and not h["refined"]:
+            return self.floor[h["rid"]]  # stuck at a rounding floor until refined
         return 0.0 if h["n"] >= self.need[h["rid"]] else 1.0
 
     def measure(self, h, r):
@@ -42,28 +57,86 @@ class FakeBackend:
         self.live -= self.bytes_of[h["rid"]]
 
 
+class RefiningBackend(FakeBackend):
+    def refine(self, h):
+        if h["refined"]:
+            return False
+        h["refined"] = True
+        self.refined.append(h["rid"])
+        return True
+
+
 def req(i, tol=0.5, max_sweeps=100):
     return Request(i, 2, 2, 4, None, None, None, None, tol=tol, max_sweeps=max_sweeps, arrival=float(i))
 
 
-def test_admission_respects_budget_and_order():
+def test_first_fit_admission_respects_budget():
     sizes = {0: 60, 1: 50, 2: 30, 3: 10}
     fb = FakeBackend(sizes, {0: 3, 1: 1, 2: 2, 3: 1})
     t = iter(range(1000))
     srv = Server(100, fb, clock=lambda: float(next(t)))
     for i in range(4):
         srv.submit(req(i))
-    srv.step()
-    # 0 (60) admitted; 1 (50) does not fit and blocks 2, 3 behind it
-    assert fb.opened[:1] == [0] and 1 not in fb.opened[:1]
+    srv.poll()
+    # 0 (60) admitted; 1 (50) does not fit; 2 (30) and 3 (10) fit behind it
+    assert fb.opened == [0, 2, 3] and [r.rid for r in srv.waiting] == [1]
     res = srv.drain()
     assert fb.peak <= 100
-    assert fb.opened == [0, 1, 2, 3]  # arrival order
+    assert fb.opened == [0, 2, 3, 1]
     assert sorted(r.rid for r in res) == [0, 1, 2, 3]
     assert all(r.converged for r in res)
-    assert fb.live == 0 and srv.in_use == 0
+    assert fb.live == 0 and srv.in_use == 0 and srv.pool.free == [(0, 100)]  # pool merged back
     for r in res:
         assert np.all(r.observables == r.rid)
+
+
+def test_head_of_queue_ages():
+    """The head may be passed over max_skip times; then it goes next."""
+    sizes = {0: 90, 1: 50, 2: 5, 3: 5, 4: 5}
+    fb = FakeBackend(sizes, {0: 4, 1: 1, 2: 50, 3: 50, 4: 50})
+    srv = Server(100, fb, max_skip=1)
+    for i in range(5):
+        srv.submit(req(i))
+    srv.poll()
+    # 0 admitted; 1 blocked; 2 passes it once; 3 and 4 must now wait behind 1
+    assert fb.opened == [0, 2]
+    srv.drain()
+    assert fb.opened.index(1) < fb.opened.index(3) < fb.opened.index(4)
+
+
+def test_requests_advance_at_their_own_pace():
+    """A request whose sweeps take many polls does not hold back another."""
+    fb = FakeBackend({0: 10, 1: 10}, {0: 3, 1: 6}, lag={0: 20, 1: 0})
+    srv = Server(100, fb)
+    srv.submit(req(0))
+    srv.submit(req(1))
+    for _ in range(15):
+        srv.poll()
+    done = {r.rid for r in srv.done}
+    assert done == {1}  # 1 finished its 6 sweeps while 0's first sweep was still running
+    srv.drain()
+    assert {r.rid for r in srv.done} == {0, 1}
+
+
+def test_pool_first_fit_and_merge():
+    from paper_2112_13184_gb300.serve import DevicePool
+    p = DevicePool(1024, 256)
+    a, b, c = p.alloc(100), p.alloc(300), p.alloc(200)
+    assert (a, b, c) == (0, 256, 768) and p.alloc(10) is None  # 256-byte granules
+    p.release(b, 300)
+    assert p.alloc(256) == 256
+    p.release(a, 100)
+    p.release(256, 256)
+    p.release(c, 200)
+    assert p.free == [(0, 1024)]
+
+
+def test_stall_triggers_refinement():
+    fb = RefiningBackend({0: 1}, {0: 5}, floor={0: 1e-8})
+    srv = Server(10, fb)
+    srv.submit(req(0, tol=1e-10))
+    res = srv.drain()
+    assert fb.refined == [0] and res[0].converged
 
 
 def test_max_sweeps_and_stats():
@@ -76,14 +149,15 @@ def test_max_sweeps_and_stats():
     assert res[1].sweeps == 2 and res[1].converged
     st = srv.stats()
     assert st["requests"] == 2 and st["converged"] == 1 and st["p99_s"] >= st["p50_s"]
+    assert st["sweeps_total"] == 7
 
 
 def test_cancel_waiting_and_active():
-    fb = FakeBackend({0: 60, 1: 60, 2: 30}, {0: 10 ** 9, 1: 1, 2: 1})
+    fb = FakeBackend({0: 60, 1: 60, 2: 50}, {0: 10 ** 9, 1: 1, 2: 1})
     srv = Server(100, fb)
     for i in range(3):
         srv.submit(req(i))
-    srv.step()  # 0 active; 1 waits (no room), 2 waits behind it
+    srv.poll()  # 0 active; 1 and 2 wait (no room for either)
     assert srv.cancel(2) and [r.rid for r in srv.waiting] == [1]
     assert srv.cancel(0)  # frees 60: 1 is admitted at once
     assert fb.closed[:1] == [0] and [a.req.rid for a in srv.active] == [1]
@@ -114,10 +188,10 @@ def test_alone_equals_mix_and_batched_equals_sequential():
     reqs = [make(j) for j in range(5)]
     alone = {}
     for r in reqs:
-        srv = Server(1 << 40, CtmBackend("mixed"))
+        srv = Server(8 << 30, CtmBackend("mixed"))
         srv.submit(r)
         alone[r.rid] = srv.drain()[0]
-    srv = Server(1 << 40, CtmBackend("mixed"))
+    srv = Server(8 << 30, CtmBackend("mixed"))
     for r in reqs:
         srv.submit(r)
     mix = {x.rid: x for x in srv.drain()}
