@@ -109,11 +109,17 @@ typedef struct {
                                and CTM_3XTF32: 1e-4) the handle switches to FP64
                                contractions for the remaining sweeps and stays
                                in FP64 afterwards                               */
+    int batch_cuts;         /* != 0: the two row cuts of a column step are processed
+                               together -- both cuts' enlarged corners stay
+                               resident (4 N^2 more doubles and, in a tensor-core
+                               mode, 8 more slice caches) and their projector
+                               SVDs run in one launch                          */
 } ctm_options;
 
 /* Defaults: chi=16, max_sweeps=100, tol=1e-10, FP64, 5 slices,
  * p=max(8,chi/8) (when rsvd_oversample<=0), q=2, cutoff 1e-12, seed 0,
- * exact_svd_max_n=256, rsvd_warm_start=1, conv_measure=0, fp64_refine=0. */
+ * exact_svd_max_n=256, rsvd_warm_start=1, conv_measure=0, fp64_refine=0,
+ * batch_cuts=1. */
 ctm_status ctm_default_options(ctm_options* opt);
 
 /* Device bytes a handle of this shape allocates (workspace included): the

@@ -82,7 +82,10 @@ struct ctm_ctx {
     double* env[4][8] = {};   // [site][which]
     // scratch
     double *X1 = nullptr, *S1 = nullptr, *S2 = nullptr, *S3 = nullptr;
-    double* E[4] = {};        // ul, ur, br, bl of the current cut
+    double* E[8] = {};        // ul, ur, br, bl of the current cut (E[4..7]: the second cut when batched)
+    // second cut's range-finder bases and SVD factors (batch_cuts)
+    double *Qm1 = nullptr, *Qb1 = nullptr, *G1 = nullptr, *Us1 = nullptr, *Ws1 = nullptr, *Sv1 = nullptr;
+    void* svd2_ws = nullptr;
     double *Pup[2] = {}, *PdnT[2] = {};
     double *Om = nullptr, *Yb = nullptr, *Zb = nullptr, *Qm = nullptr, *Qm2 = nullptr, *Qb = nullptr;
     double *Rb = nullptr, *G = nullptr, *Us = nullptr, *Ws = nullptr, *Sv = nullptr, *inv = nullptr;
@@ -97,7 +100,7 @@ struct ctm_ctx {
     // slices of the four enlarged corners (x plain / transposed), reused by
     // every corner apply of a cut; invalidated by any write to the corner
     struct SliceCache { const double* ptr = nullptr; bool trans = false; void* buf = nullptr; bool valid = false; };
-    SliceCache ozc[8];
+    SliceCache ozc[16];
     // warm start of the range finder: previous sweep's right basis per cut
     double* warmV[16] = {};
     bool warm_valid[16] = {};
@@ -229,7 +232,8 @@ size_t footprint(int d, int D, const ctm_options& o) {
     dbl += 16 * z.C + 16 * z.T;      // environments
     dbl += z.T;                      // X1
     dbl += 2 * z.open + (size_t)d * z.NN;  // S1, S3 (open RDM size), S2
-    dbl += 4 * z.NN;                 // E
+    dbl += (o.batch_cuts ? 8 : 4) * z.NN;  // E (both cuts with batch_cuts)
+    if (o.batch_cuts) dbl += 2 * z.Nk + 3 * z.kk + (size_t)k;  // second cut's Q, Q_b, G, U', W, S
     dbl += 4 * z.Nchi;               // Pup, PdnT
     dbl += 6 * z.Nk;                 // Om, Y, Z, Qm, Qm2, Qb
     dbl += 4 * z.kk + 2 * (size_t)k; // Rb, G, Us, Ws, Sv, inv
@@ -241,6 +245,7 @@ size_t footprint(int d, int D, const ctm_options& o) {
     if (o.rsvd_warm_start && k < N) dbl += 16 * z.Nk;  // warm-start bases
     size_t bytes = dbl * sizeof(double);
     bytes += qr_ws_bytes(N, k) + svd_ws_bytes(k) + svals_ws_bytes(chi, 16);
+    if (o.batch_cuts) bytes += svd2_ws_bytes(k);
     bytes += 64 * sizeof(unsigned long long) + 64 + 64 * 256;
     bytes += 256 * 256;  // 256-byte alignment of up to 256 buffers carved from an arena
     bytes += sizeof(double) * (ctm::dot_ws_doubles() + 8);
@@ -248,7 +253,7 @@ size_t footprint(int d, int D, const ctm_options& o) {
     if (mode >= 0) {
         const int s = tc_slices_of(o);
         const OzBounds z = oz_bounds(d, D, chi, k, s, mode);
-        bytes += z.a + z.b + z.w + 3 * 256 + 8 * tc_split_bytes(N, N, mode, s);
+        bytes += z.a + z.b + z.w + 3 * 256 + (o.batch_cuts ? 16 : 8) * tc_split_bytes(N, N, mode, s);
     }
     return bytes;
 }
@@ -368,8 +373,8 @@ void slices_written(ctm_ctx* h, const double* p) {
 }
 int slice_slot(ctm_ctx* h, const double* A, bool tA, int M, int K) {
     if (!h->ozc[0].buf || M != h->N || K != h->N) return -1;
-    for (int c = 0; c < 4; ++c)
-        if (A == h->E[c]) return 2 * c + (tA ? 1 : 0);
+    for (int c = 0; c < 8; ++c)
+        if (A && A == h->E[c]) return 2 * c + (tA ? 1 : 0);
     return -1;
 }
 // operand slices of the handle's scheme for an R x K operand on strided views
@@ -550,69 +555,103 @@ ctm_status enlarged_corner(ctm_ctx* h, int i, int c, double* out) {
 // ----------------------------------------------------------------------------
 // randomised SVD of M = H_u^T H_d and the projectors of one cut
 // ----------------------------------------------------------------------------
-ctm_status applyM(ctm_ctx* h, const double* X, double* out, int cols) {
+// E: the four enlarged corners ul, ur, br, bl of the cut
+ctm_status applyM(ctm_ctx* h, double* const* E, const double* X, double* out, int cols) {
     ProfTag tg(h, "rsvd.apply");
     const int N = h->N;
-    CKS(gemm(h, true, false, N, cols, N, h->E[2], N, X, cols, h->t1, cols));      // E_br^T X
-    CKS(gemm(h, true, false, N, cols, N, h->E[3], N, h->t1, cols, h->t2, cols));  // E_bl^T
-    CKS(gemm(h, true, false, N, cols, N, h->E[0], N, h->t2, cols, h->t1, cols));  // E_ul^T
-    CKS(gemm(h, true, false, N, cols, N, h->E[1], N, h->t1, cols, out, cols));    // E_ur^T
+    CKS(gemm(h, true, false, N, cols, N, E[2], N, X, cols, h->t1, cols));      // E_br^T X
+    CKS(gemm(h, true, false, N, cols, N, E[3], N, h->t1, cols, h->t2, cols));  // E_bl^T
+    CKS(gemm(h, true, false, N, cols, N, E[0], N, h->t2, cols, h->t1, cols));  // E_ul^T
+    CKS(gemm(h, true, false, N, cols, N, E[1], N, h->t1, cols, out, cols));    // E_ur^T
     return CTM_OK;
 }
-ctm_status applyMT(ctm_ctx* h, const double* X, double* out, int cols) {
+ctm_status applyMT(ctm_ctx* h, double* const* E, const double* X, double* out, int cols) {
     ProfTag tg(h, "rsvd.apply");
     const int N = h->N;
-    CKS(gemm(h, false, false, N, cols, N, h->E[1], N, X, cols, h->t1, cols));      // E_ur X
-    CKS(gemm(h, false, false, N, cols, N, h->E[0], N, h->t1, cols, h->t2, cols));  // E_ul
-    CKS(gemm(h, false, false, N, cols, N, h->E[3], N, h->t2, cols, h->t1, cols));  // E_bl
-    CKS(gemm(h, false, false, N, cols, N, h->E[2], N, h->t1, cols, out, cols));    // E_br
+    CKS(gemm(h, false, false, N, cols, N, E[1], N, X, cols, h->t1, cols));      // E_ur X
+    CKS(gemm(h, false, false, N, cols, N, E[0], N, h->t1, cols, h->t2, cols));  // E_ul
+    CKS(gemm(h, false, false, N, cols, N, E[3], N, h->t2, cols, h->t1, cols));  // E_bl
+    CKS(gemm(h, false, false, N, cols, N, E[2], N, h->t1, cols, out, cols));    // E_br
     return CTM_OK;
 }
 
-// cut: (frame, column, row) index 0..15, keys the warm-start basis
-ctm_status projectors(ctm_ctx* h, int slot, int cut) {
+// what one cut keeps from its range finder to its projectors
+struct CutBufs {
+    double* const* E;
+    double *Qm, *Qb, *G, *Us, *Ws, *Sv;
+};
+CutBufs cut_bufs(ctm_ctx* h, int which) {
+    if (which == 0) return CutBufs{h->E, h->Qm, h->Qb, h->G, h->Us, h->Ws, h->Sv};
+    return CutBufs{h->E + 4, h->Qm1, h->Qb1, h->G1, h->Us1, h->Ws1, h->Sv1};
+}
+
+// cut: (frame, column, row) index 0..15, keys the warm-start basis.
+// Range finder of M = H_u^T H_d up to the small factor G = R_b^T.
+ctm_status range_finder(ctm_ctx* h, int cut, const CutBufs& c) {
     ProfTag tg(h, "projector");
-    const int N = h->N, k = h->k, chi = h->chi;
+    const int N = h->N, k = h->k;
     const bool warm_on = h->opt.rsvd_warm_start && k < N;
     const bool warm = warm_on && h->warm_valid[cut];
     const int q = (k == N || warm) ? 0 : h->q;
     const double* Om = h->Om;
     if (warm) Om = h->warmV[cut];  // one more subspace iteration from last sweep's basis
     else CK(ctm::rng_normal(h->Om, (size_t)N * k, h->opt.seed, h->rng_counter++, h->stream));
-    CKS(applyM(h, Om, h->Yb, k));
+    CKS(applyM(h, c.E, Om, h->Yb, k));
     // Householder QR for every basis: a Gram-based (Cholesky) QR resolves
     // only directions above ~1e-8 of the largest, while the 1e-12 cutoff keeps
     // directions down to 1e-12; with a warm basis that lags a still-changing
     // environment that loss stopped the D=8, chi=128 iteration converging.
-    CKS(qr_(h, h->Yb, h->Qm, h->Rb));
+    CKS(qr_(h, h->Yb, c.Qm, h->Rb));
     for (int it = 0; it < q; ++it) {
-        CKS(applyMT(h, h->Qm, h->Zb, k));
+        CKS(applyMT(h, c.E, c.Qm, h->Zb, k));
         CKS(qr_(h, h->Zb, h->Qm2, h->Rb));
-        CKS(applyM(h, h->Qm2, h->Yb, k));
-        CKS(qr_(h, h->Yb, h->Qm, h->Rb));
+        CKS(applyM(h, c.E, h->Qm2, h->Yb, k));
+        CKS(qr_(h, h->Yb, c.Qm, h->Rb));
     }
     // B^T = M^T Q = Q_b R_b  ->  B = R_b^T Q_b^T ; SVD(R_b^T) = U' S W^T
-    CKS(applyMT(h, h->Qm, h->Zb, k));
-    CKS(qr_(h, h->Zb, h->Qb, h->Rb));
-    CKS(perm(h, h->Rb, h->G, {k, k}, {1, 0}));
-    CKS(svd_(h));
+    CKS(applyMT(h, c.E, c.Qm, h->Zb, k));
+    CKS(qr_(h, h->Zb, c.Qb, h->Rb));
+    return perm(h, h->Rb, c.G, {k, k}, {1, 0});
+}
+
+// Projectors of a cut from the SVD of its small factor.
+ctm_status finish_projectors(ctm_ctx* h, int slot, int cut, const CutBufs& c) {
+    ProfTag tg(h, "projector");
+    const int N = h->N, k = h->k, chi = h->chi;
+    const bool warm_on = h->opt.rsvd_warm_start && k < N;
     // U = Q U'[:, :chi].  V = Q_b W over all k columns, sorted by singular
     // value: its first chi columns are the projector's V, and the whole basis
     // (the span of Q_b) starts this cut's range finder in the next sweep,
     // where it leaves R_b close to diagonal once the environment settles, so
     // that the Jacobi SVD starts near its quadratic phase.
     double* Vf = warm_on ? h->warmV[cut] : h->Vc;
-    CKS(gemm(h, false, false, N, chi, k, h->Qm, k, h->Us, k, h->Uc, chi));
-    CKS(gemm(h, false, false, N, k, k, h->Qb, k, h->Ws, k, Vf, k));
+    CKS(gemm(h, false, false, N, chi, k, c.Qm, k, c.Us, k, h->Uc, chi));
+    CKS(gemm(h, false, false, N, k, k, c.Qb, k, c.Ws, k, Vf, k));
     if (warm_on) h->warm_valid[cut] = true;
-    CK(ctm::inv_sqrt_cut(h->Sv, h->inv, chi, h->opt.sv_cutoff_rel, h->stream));
+    CK(ctm::inv_sqrt_cut(c.Sv, h->inv, chi, h->opt.sv_cutoff_rel, h->stream));
     // P_up = E_bl^T (E_br^T V) S^-1/2 ; P_dn^T = E_ul (E_ur U) S^-1/2
-    CKS(gemm(h, true, false, N, chi, N, h->E[2], N, Vf, k, h->t1, chi));
-    CKS(gemm(h, true, false, N, chi, N, h->E[3], N, h->t1, chi, h->Pup[slot], chi));
+    CKS(gemm(h, true, false, N, chi, N, c.E[2], N, Vf, k, h->t1, chi));
+    CKS(gemm(h, true, false, N, chi, N, c.E[3], N, h->t1, chi, h->Pup[slot], chi));
     CK(ctm::scale_cols(h->Pup[slot], N, chi, chi, h->inv, h->stream));
-    CKS(gemm(h, false, false, N, chi, N, h->E[1], N, h->Uc, chi, h->t1, chi));
-    CKS(gemm(h, false, false, N, chi, N, h->E[0], N, h->t1, chi, h->PdnT[slot], chi));
+    CKS(gemm(h, false, false, N, chi, N, c.E[1], N, h->Uc, chi, h->t1, chi));
+    CKS(gemm(h, false, false, N, chi, N, c.E[0], N, h->t1, chi, h->PdnT[slot], chi));
     CK(ctm::scale_cols(h->PdnT[slot], N, chi, chi, h->inv, h->stream));
+    return CTM_OK;
+}
+
+ctm_status projectors(ctm_ctx* h, int slot, int cut) {
+    const CutBufs c = cut_bufs(h, 0);
+    CKS(range_finder(h, cut, c));
+    CKS(svd_(h));
+    return finish_projectors(h, slot, cut, c);
+}
+
+// both cuts' SVDs in one launch (two Jacobi clusters)
+ctm_status svd2_(ctm_ctx* h, const CutBufs& a, const CutBufs& b) {
+    ProfTag tg(h, "svd");
+    const size_t ev = prof_begin(h);
+    CK(ctm::svd2(a.G, b.G, h->k, a.Us, a.Sv, a.Ws, b.Us, b.Sv, b.Ws, h->svd2_ws, h->stream, h->flag + 2));
+    prof_end(h, ev, P_SVD, 0.0, 0.0);
     return CTM_OK;
 }
 
@@ -627,14 +666,22 @@ ctm_status normalise_into(ctm_ctx* h, const double* src, double* dst, size_t n, 
 // absorb column x of frame m into the left boundary of column x+1
 ctm_status left_move(ctm_ctx* h, int m, int x) {
     const int chi = h->chi, N = h->N, D = h->D;
+    const bool both = h->E[4] != nullptr;  // batch_cuts: corners of both cuts resident
     for (int y = 0; y < 2; ++y) {
         const int tl = FM.site(m, x, y + 1), tr = FM.site(m, x + 1, y + 1);
         const int br = FM.site(m, x + 1, y), bl = FM.site(m, x, y);
-        CKS(enlarged_corner(h, tl, m + 0, h->E[0]));
-        CKS(enlarged_corner(h, tr, m + 1, h->E[1]));
-        CKS(enlarged_corner(h, br, m + 2, h->E[2]));
-        CKS(enlarged_corner(h, bl, m + 3, h->E[3]));
-        CKS(projectors(h, y, ((m & 3) * 2 + x) * 2 + y));
+        double* const* E = both ? h->E + 4 * y : h->E;
+        CKS(enlarged_corner(h, tl, m + 0, E[0]));
+        CKS(enlarged_corner(h, tr, m + 1, E[1]));
+        CKS(enlarged_corner(h, br, m + 2, E[2]));
+        CKS(enlarged_corner(h, bl, m + 3, E[3]));
+        const int cut = ((m & 3) * 2 + x) * 2 + y;
+        if (!both) CKS(projectors(h, y, cut));
+        else CKS(range_finder(h, cut, cut_bufs(h, y)));
+    }
+    if (both) {
+        CKS(svd2_(h, cut_bufs(h, 0), cut_bufs(h, 1)));
+        for (int y = 0; y < 2; ++y) CKS(finish_projectors(h, y, ((m & 3) * 2 + x) * 2 + y, cut_bufs(h, y)));
     }
     ProfTag tg(h, "absorb");
     for (int y = 0; y < 2; ++y) {
@@ -1256,6 +1303,7 @@ ctm_status ctm_default_options(ctm_options* o) {
     o->rsvd_warm_start = 1;
     o->conv_measure = 0;
     o->fp64_refine = 0;
+    o->batch_cuts = 1;
     return CTM_OK;
 }
 
@@ -1347,7 +1395,12 @@ ctm_status create(int Lx, int Ly, int d, int D, const ctm_options* o, void* stre
     A_(&h->S1, z.open);
     A_(&h->S3, z.open);
     A_(&h->S2, (size_t)d * z.NN);
-    for (int c = 0; c < 4; ++c) A_(&h->E[c], z.NN);
+    for (int c = 0; c < (o->batch_cuts ? 8 : 4); ++c) A_(&h->E[c], z.NN);
+    if (o->batch_cuts) {
+        A_(&h->Qm1, z.Nk); A_(&h->Qb1, z.Nk); A_(&h->G1, z.kk); A_(&h->Us1, z.kk); A_(&h->Ws1, z.kk);
+        A_(&h->Sv1, h->k);
+        if (st == CTM_OK) st = alloc(h, &h->svd2_ws, svd2_ws_bytes(h->k));
+    }
     for (int s = 0; s < 2; ++s) { A_(&h->Pup[s], z.Nchi); A_(&h->PdnT[s], z.Nchi); }
     A_(&h->Om, z.Nk); A_(&h->Yb, z.Nk); A_(&h->Zb, z.Nk); A_(&h->Qm, z.Nk); A_(&h->Qm2, z.Nk); A_(&h->Qb, z.Nk);
     A_(&h->Rb, z.kk); A_(&h->G, z.kk); A_(&h->Us, z.kk); A_(&h->Ws, z.kk);
@@ -1380,7 +1433,7 @@ ctm_status create(int Lx, int Ly, int d, int D, const ctm_options* o, void* stre
         st = alloc(h, &h->ozA, h->ozA_n);
         if (st == CTM_OK) st = alloc(h, &h->ozB, h->ozB_n);
         if (st == CTM_OK) st = alloc(h, &h->ozW, h->ozW_n);
-        for (int c = 0; c < 8 && st == CTM_OK; ++c) {
+        for (int c = 0; c < (o->batch_cuts ? 16 : 8) && st == CTM_OK; ++c) {
             h->ozc[c].ptr = h->E[c / 2];
             h->ozc[c].trans = (c & 1) != 0;
             st = alloc(h, &h->ozc[c].buf, tc_split_bytes(h->N, h->N, tmode, tsl));

@@ -57,6 +57,11 @@ size_t svd_ws_bytes(int k);
 // iteration still rotated in its last allowed sweep
 cudaError_t svd(const double* G, int k, double* U, double* S, double* V, void* ws, cudaStream_t s,
                 int* status = nullptr);
+// two independent SVDs of k x k matrices in one Jacobi launch (one cluster
+// each); ws: svd2_ws_bytes(k); *status as for svd()
+size_t svd2_ws_bytes(int k);
+cudaError_t svd2(const double* G0, const double* G1, int k, double* U0, double* S0, double* V0, double* U1,
+                 double* S1, double* V1, void* ws, cudaStream_t s, int* status = nullptr);
 // svd() with its workspace in a static device array (k <= svd_noalloc_max_k())
 int svd_noalloc_max_k();
 cudaError_t svd_noalloc(const double* G, int k, double* U, double* S, double* V, cudaStream_t s);

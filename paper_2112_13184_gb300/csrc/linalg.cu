@@ -1063,6 +1063,41 @@ cudaError_t small_eig(const double* H, int m, int ldh, double period, double* ou
     return cudaGetLastError();
 }
 
+// Two independent SVDs in one Jacobi launch (two clusters); the layout of
+// svd() per matrix: status word, then G^T, W^T, norms, off-diagonal maxima
+size_t svd2_ws_bytes(int k) {
+    return 256 + sizeof(double) * 2 * (2 * (size_t)k * k + k) + sizeof(unsigned long long) * 2 * JACOBI_MAX_SWEEPS +
+           256;
+}
+
+cudaError_t svd2(const double* G0, const double* G1, int k, double* U0, double* S0, double* V0, double* U1,
+                 double* S1, double* V1, void* ws, cudaStream_t s, int* status) {
+    if (k <= 0 || k > 1024) return cudaErrorInvalidValue;
+    int* st = (int*)ws;
+    double* Gt = (double*)((char*)ws + 256);        // [2][k][k]
+    double* Wt = Gt + 2 * (size_t)k * k;             // [2][k][k]
+    double* nrm = Wt + 2 * (size_t)k * k;            // [2][k]
+    unsigned long long* off = (unsigned long long*)(nrm + 2 * (size_t)k);  // [2][sweeps]
+    cudaError_t e = cudaMemsetAsync(off, 0, sizeof(unsigned long long) * 2 * JACOBI_MAX_SWEEPS, s);
+    if (e) return e;
+    e = cudaMemsetAsync(st, 0, sizeof(int), s);
+    if (e) return e;
+    ++g_launches;
+    k_transpose_batch<<<grid_for((size_t)k * k), 256, 0, s>>>(G0, Gt, k, 1);
+    ++g_launches;
+    k_transpose_batch<<<grid_for((size_t)k * k), 256, 0, s>>>(G1, Gt + (size_t)k * k, k, 1);
+    ++g_launches;
+    k_eye_batch<<<grid_for(2 * (size_t)k * k), 256, 0, s>>>(Wt, k, 2);
+    const int n = k + (k & 1);
+    e = jacobi(Gt, Wt, k, n, 2, off, nrm, status ? status : st, s);
+    if (e) return e;
+    ++g_launches;
+    k_jacobi_finish<<<1, 256, sizeof(double) * k, s>>>(Gt, Wt, k, U0, S0, V0);
+    ++g_launches;
+    k_jacobi_finish<<<1, 256, sizeof(double) * k, s>>>(Gt + (size_t)k * k, Wt + (size_t)k * k, k, U1, S1, V1);
+    return cudaGetLastError();
+}
+
 size_t svals_ws_bytes(int k, int nb) {
     return sizeof(double) * (size_t)nb * ((size_t)k * k + k) + sizeof(unsigned long long) * JACOBI_MAX_SWEEPS * nb +
            256;

@@ -36,7 +36,8 @@ class ctm_options(ctypes.Structure):
     _fields_ = [("chi", c_int), ("max_sweeps", c_int), ("tol", c_double), ("precision", c_int),
                 ("ozaki_slices", c_int), ("rsvd_oversample", c_int), ("rsvd_power_iters", c_int),
                 ("sv_cutoff_rel", c_double), ("seed", ctypes.c_uint64), ("exact_svd_max_n", c_int),
-                ("rsvd_warm_start", c_int), ("conv_measure", c_int), ("fp64_refine", c_int)]
+                ("rsvd_warm_start", c_int), ("conv_measure", c_int), ("fp64_refine", c_int),
+                ("batch_cuts", c_int)]
 
 
 class ctm_profile_data(ctypes.Structure):

@@ -347,3 +347,23 @@ def test_mixed_converges_in_loop_measure(ctm):
         out[prec] = np.array([c.measure2(i, dx, dy, q["op2"]) for (i, dx, dy) in I.SQUARE_2X2_BONDS])
         c.close()
     assert np.max(np.abs(out["mixed"] - out["fp64"])) < 1e-8
+
+
+@pytest.mark.parametrize("precision", ["fp64", "mixed"])
+def test_batched_cuts_equal_one_at_a_time(ctm, precision):
+    """batch_cuts = 1 (both row cuts' corners resident, their SVDs in one
+    launch) runs the same arithmetic per cut as batch_cuts = 0: the
+    environments agree bit for bit, through cold and warm randomised sweeps."""
+    w = I.workload("neel_d2_D3_chi16")
+    prec = ctm.CTM_OZAKI_BF16 if precision == "mixed" else ctm.CTM_FP64
+    out = []
+    for batch in (0, 1):
+        c = ctm.CTMRG(2, 3, 16, precision=prec, exact_svd_max_n=0, batch_cuts=batch)
+        c.set_tensors(w["As"])
+        c.set_envs(w["envs"])
+        c.sweep(4)
+        out.append(c.get_envs())
+        c.close()
+    for ea, eb in zip(*out):
+        for k in ea:
+            np.testing.assert_array_equal(ea[k], eb[k])
