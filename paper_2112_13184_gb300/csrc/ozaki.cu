@@ -121,6 +121,12 @@ __device__ __forceinline__ double scale_pow2(double v, int k) {
     return ldexp(v, k);
 }
 
+// Z * 2^E outside the normal FP64 range (rare): kept out of line so that its
+// FP64 conversion and scaling are not if-converted into every element
+__device__ __noinline__ double i64_ldexp_slow(long long Z, int E) {
+    return ldexp((double)Z, E);
+}
+
 // Z * 2^E as an FP64 number (round to nearest even) with integer operations
 // only: GB300's FP64 pipe is too slow to spend on every output element.
 __device__ __forceinline__ double i64_ldexp(long long Z, int E) {
@@ -143,7 +149,7 @@ __device__ __forceinline__ double i64_ldexp(long long Z, int E) {
         mant = m << (-sh);
     }
     const int be = E + sh + 52 + 1023;  // value = mant 2^(E+sh), mant in [2^52, 2^53)
-    if (be <= 0 || be >= 2047) return ldexp(neg ? -(double)m : (double)m, E);  // outside the normal range
+    if (be <= 0 || be >= 2047) return i64_ldexp_slow(Z, E);  // outside the normal range
     return __longlong_as_double((long long)((neg << 63) | ((unsigned long long)be << 52) | (mant & ((1ull << 52) - 1))));
 }
 
@@ -164,12 +170,16 @@ __device__ __forceinline__ long long f32_fixed(float f, int k) {
 // C = 2^(eA+eB-16) (S0 + S1/256 + F).  With T = 256 S0 + S1 (exact; |T| <
 // 2^39 for K <= 16384 per split) and F kept to 2^-28 of an S0 unit (below
 // 2^-44 of max|row| max|col|), Z = 2^20 T + round(2^28 F) is an exact int64
-// and C = Z 2^(eA+eB-44).  escale = eA + eB - 16.
+// and C = Z 2^(eA+eB-44).  escale = eA + eB - 16.  round(2^28 F) is taken
+// from F's bit pattern: an FP32 -> int64 conversion instruction issues on
+// the FP64 pipe, which GB300 runs at 2 lanes per clock per SM.
 __device__ __forceinline__ double assemble(int S0, int S1, float F, int escale) {
     const long long T = (long long)S0 * 256 + (long long)S1;
-    const long long Z = T * (1ll << 20) + __float2ll_rn(F * 268435456.0f);  // F 2^28 < 2^62
+    const long long Z = T * (1ll << 20) + f32_fixed(F, 28);  // F 2^28 < 2^62
     return i64_ldexp(Z, escale - 28);
 }
+
+__device__ __noinline__ double f32_ldexp_slow(float f, int E) { return ldexp((double)f, E); }
 
 // f 2^E as an FP64 number for an FP32 f (the accumulator of the FP32-
 // accumulated modes), built from the bit pattern: the exponent is rebiased
@@ -180,7 +190,7 @@ __device__ __forceinline__ double f32_scaled(float f, int E) {
     if (ex == 0) return 0.0;                                      // zero or FP32 denormal
     if (ex == 255) return __longlong_as_double(0x7ff8000000000000ll);  // Inf/NaN accumulator
     const int be = ex - 127 + 1023 + E;
-    if (be <= 0 || be >= 2047) return ldexp((double)f, E);        // outside the normal FP64 range
+    if (be <= 0 || be >= 2047) return f32_ldexp_slow(f, E);       // outside the normal FP64 range
     return __longlong_as_double((long long)(((unsigned long long)(b >> 31) << 63) |
                                             ((unsigned long long)be << 52) |
                                             ((unsigned long long)(b & 0x7fffffu) << 29)));
@@ -895,9 +905,10 @@ __global__ void __launch_bounds__(THREADS, 1)
                     if (m >= g.M || n >= g.N) continue;
                     double v = f32_scaled(F[jb][j], ea + eb - 2 * dbits);
                     if (ea > 1024 || eb > 1024) v = __longlong_as_double(0x7ff8000000000000ll);  // non-finite operand
-                    if (!unit_alpha) v *= g.alpha;
                     double* cp = crow + coff;
-                    *cp = zero_beta ? v : fma(g.beta, *cp, v);
+                    // uniform branch: no FP64 arithmetic issued when alpha = 1, beta = 0
+                    if (unit_alpha && zero_beta) *cp = v;
+                    else *cp = zero_beta ? v * g.alpha : fma(g.beta, *cp, v * g.alpha);
                 }
             }
         }
@@ -936,17 +947,33 @@ __global__ void __launch_bounds__(THREADS, 1)
                 const long long coff_l = nl < g.N ? view_offset32(g.out_c, (unsigned)nl) : 0;
                 const int eb_l = nl < g.N ? g.eB[nl] : 0;
                 double* crow = g.C + (m < g.M ? view_offset32(g.out_r, (unsigned)m) : 0);
+                // alpha = 1, beta = 0 (every product of the sweep) takes a loop
+                // with no FP64 arithmetic at all: the branch is uniform, so
+                // the scaling is not issued under a predicate per element
+                if (unit_alpha && zero_beta) {
 #pragma unroll
-                for (int j = 0; j < 16; ++j) {
-                    const long long coff = __shfl_sync(0xffffffffu, coff_l, j);
-                    const int eb = __shfl_sync(0xffffffffu, eb_l, j);
-                    const int n = n0 + b * 16 + j;
-                    if (m >= g.M || n >= g.N) continue;
-                    double v = assemble(S0[jb][j], S1[jb][j], Fs[jb][j], ea + eb - 16);
-                    if (ea > 1024 || eb > 1024) v = __longlong_as_double(0x7ff8000000000000ll);  // non-finite operand
-                    if (!unit_alpha) v *= g.alpha;
-                    double* cp = crow + coff;
-                    *cp = zero_beta ? v : fma(g.beta, *cp, v);
+                    for (int j = 0; j < 16; ++j) {
+                        const long long coff = __shfl_sync(0xffffffffu, coff_l, j);
+                        const int eb = __shfl_sync(0xffffffffu, eb_l, j);
+                        const int n = n0 + b * 16 + j;
+                        if (m >= g.M || n >= g.N) continue;
+                        double v = assemble(S0[jb][j], S1[jb][j], Fs[jb][j], ea + eb - 16);
+                        if (ea > 1024 || eb > 1024) v = __longlong_as_double(0x7ff8000000000000ll);  // non-finite operand
+                        crow[coff] = v;
+                    }
+                } else {
+#pragma unroll
+                    for (int j = 0; j < 16; ++j) {
+                        const long long coff = __shfl_sync(0xffffffffu, coff_l, j);
+                        const int eb = __shfl_sync(0xffffffffu, eb_l, j);
+                        const int n = n0 + b * 16 + j;
+                        if (m >= g.M || n >= g.N) continue;
+                        double v = assemble(S0[jb][j], S1[jb][j], Fs[jb][j], ea + eb - 16);
+                        if (ea > 1024 || eb > 1024) v = __longlong_as_double(0x7ff8000000000000ll);
+                        v *= g.alpha;
+                        double* cp = crow + coff;
+                        *cp = zero_beta ? v : fma(g.beta, *cp, v);
+                    }
                 }
             } else {
                 const size_t row = ((size_t)blockIdx.z * g.Mpad + m) * g.Npad + n0 + b * 16;
