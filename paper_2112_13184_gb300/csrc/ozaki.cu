@@ -205,6 +205,12 @@ __device__ __forceinline__ unsigned long long abs_bits(double x) {
 __device__ __forceinline__ unsigned long long umax64(unsigned long long a, unsigned long long b) {
     return a > b ? a : b;
 }
+// row_exponent of the bit pattern of max|x| (integer operations only)
+__device__ __forceinline__ int row_exponent_bits(unsigned long long mb) {
+    if ((mb & 0x7fffffffffffffffull) == 0) return 0;
+    const int E = (int)((mb >> 52) & 0x7ff);
+    return E == 0 ? -1022 : E - 1022;
+}
 // exponent e with max|x| < 2^e (0 for an all-zero row; 1025 when the row
 // holds an infinity or a NaN, which the products turn into NaN outputs)
 __device__ __forceinline__ int row_exponent(double mx) {
@@ -217,8 +223,12 @@ __device__ __forceinline__ int row_exponent(double mx) {
 // lie in [-128, 127] (Y = 256 Y' + d with Y' = floor((Y + 128) / 256)), d[0]
 // carries the sign and the top.  Every index of d is static (unrolled over
 // MAX_S), so d stays in registers.
+__device__ __forceinline__ void digits_bits(unsigned long long b, int e, int s, int* d);
 __device__ __forceinline__ void digits(double x, int e, int s, int* d) {
-    const unsigned long long b = (unsigned long long)__double_as_longlong(x);
+    digits_bits((unsigned long long)__double_as_longlong(x), e, s, d);
+}
+// the same from the FP64 bit pattern b
+__device__ __forceinline__ void digits_bits(unsigned long long b, int e, int s, int* d) {
     int ex = (int)((b >> 52) & 0x7ff);
     unsigned long long mant = b & ((1ull << 52) - 1);
     if (ex == 0) ex = 1;
@@ -440,6 +450,22 @@ __device__ __forceinline__ void slice8_pack(const double* v, int e, int s, uint4
         }
     }
 }
+// slice8_pack of eight FP64 bit patterns
+__device__ __forceinline__ void slice8_pack_bits(const unsigned long long* vb, int e, int s, uint4* q) {
+    int d[8][MAX_S];
+#pragma unroll
+    for (int u = 0; u < 8; ++u) digits_bits(vb[u], e, s, d[u]);
+#pragma unroll
+    for (int t = 0; t < MAX_S; ++t) {
+        if (t < s) {
+            const float sc = __int_as_float((127 - 8 * t) << 23);  // 2^(-8t)
+            q[t].x = bf2_bits(small_int_f32(d[0][t]) * sc, small_int_f32(d[1][t]) * sc);
+            q[t].y = bf2_bits(small_int_f32(d[2][t]) * sc, small_int_f32(d[3][t]) * sc);
+            q[t].z = bf2_bits(small_int_f32(d[4][t]) * sc, small_int_f32(d[5][t]) * sc);
+            q[t].w = bf2_bits(small_int_f32(d[6][t]) * sc, small_int_f32(d[7][t]) * sc);
+        }
+    }
+}
 __device__ __forceinline__ void slice8_store(const double* v, int e, int s, __nv_bfloat16* dst, size_t plane) {
     uint4 q[MAX_S];
     slice8_pack(v, e, s, q);
@@ -460,28 +486,32 @@ __global__ void __launch_bounds__(256) k_split_rows_reg(const double* __restrict
     const int g = threadIdx.x / TPR, j = threadIdx.x % TPR;
     const int r = blockIdx.x * RPB + g;
     const bool live = r < R;
-    const double* xr = X + (live ? (long long)r * rs : 0);
+    // the row is held as FP64 bit patterns: kept as doubles, every value
+    // cost one FP64-pipe instruction (GB300 issues those at 2 lanes per
+    // clock per SM), and nothing here needs FP64 arithmetic
+    const unsigned long long* xr =
+        reinterpret_cast<const unsigned long long*>(X) + (live ? (long long)r * rs : 0);
     const int nch = K8 >> 3;
-    double v[4][8];
+    unsigned long long v[4][8];
     unsigned long long mb = 0;
 #pragma unroll
     for (int i = 0; i < 4; ++i) {
         const int c = j + i * TPR;
         const int k0 = c * 8;
         if (VEC && live && c < nch && k0 + 8 <= K) {
-            const double2* p2 = reinterpret_cast<const double2*>(xr + k0);
+            const ulonglong2* p2 = reinterpret_cast<const ulonglong2*>(xr + k0);
 #pragma unroll
             for (int h = 0; h < 4; ++h) {
-                const double2 w = __ldcs(p2 + h);
+                const ulonglong2 w = __ldcs(p2 + h);
                 v[i][2 * h] = w.x;
                 v[i][2 * h + 1] = w.y;
             }
         } else {
 #pragma unroll
-            for (int u = 0; u < 8; ++u) v[i][u] = (live && c < nch && k0 + u < K) ? __ldcs(xr + k0 + u) : 0.0;
+            for (int u = 0; u < 8; ++u) v[i][u] = (live && c < nch && k0 + u < K) ? __ldcs(xr + k0 + u) : 0ull;
         }
 #pragma unroll
-        for (int u = 0; u < 8; ++u) mb = umax64(mb, abs_bits(v[i][u]));
+        for (int u = 0; u < 8; ++u) mb = umax64(mb, v[i][u] & 0x7fffffffffffffffull);
     }
     if (TPR <= 32) {
 #pragma unroll
@@ -498,13 +528,20 @@ __global__ void __launch_bounds__(256) k_split_rows_reg(const double* __restrict
         for (int q = 0; q < WPR; ++q) mb = umax64(mb, red[g * WPR + q]);
     }
     if (!live) return;
-    const int e = row_exponent(__longlong_as_double((long long)mb));
+    const int e = row_exponent_bits(mb);
     if (j == 0) ex[r] = e;
     const size_t plane = (size_t)R * K8;
 #pragma unroll
     for (int i = 0; i < 4; ++i) {
         const int c = j + i * TPR;
-        if (c < nch) slice8_store(v[i], e, s, out + (size_t)r * K8 + (size_t)c * 8, plane);
+        if (c < nch) {
+            uint4 q[MAX_S];
+            slice8_pack_bits(v[i], e, s, q);
+            __nv_bfloat16* dst = out + (size_t)r * K8 + (size_t)c * 8;
+#pragma unroll
+            for (int t = 0; t < MAX_S; ++t)
+                if (t < s) *reinterpret_cast<uint4*>(dst + t * plane) = q[t];
+        }
     }
 }
 
