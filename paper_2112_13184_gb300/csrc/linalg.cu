@@ -225,9 +225,10 @@ __global__ void __launch_bounds__(PQR_THREADS) k_qr_persistent(const double* __r
                                                                double* __restrict__ P, double* __restrict__ Ajg,
                                                                unsigned* bar, int* err, long long limit) {
     extern __shared__ double sm[];
-    double* S = sm;                       // panel slab [k][nr]: R above, reflectors below the diagonal
-    double* Qs = S + (size_t)k * nr;      // Q slab [k][nr]
-    double* tot = Qs + (size_t)k * nr;    // totals of the current step [k]
+    const int ld = nr | 1;                // odd column stride: a thread per column reads without bank conflicts
+    double* S = sm;                       // panel slab [k][ld]: R above, reflectors below the diagonal
+    double* Qs = S + (size_t)k * ld;      // Q slab [k][ld]
+    double* tot = Qs + (size_t)k * ld;    // totals of the current step [k]
     double* wv = tot + k;                 // update weights [k]
     double* tau_s = wv + k;               // [k]
     double* beta_s = tau_s + k;           // [k]
@@ -239,24 +240,27 @@ __global__ void __launch_bounds__(PQR_THREADS) k_qr_persistent(const double* __r
 
     for (int t = threadIdx.x; t < k * nr; t += blockDim.x) {
         const int c = t / nr, rl = t - c * nr;
-        S[t] = rl < nrl ? Y[(size_t)(r0 + rl) * k + c] : 0.0;
-        Qs[t] = (rl < nrl && r0 + rl == c) ? 1.0 : 0.0;
+        S[(size_t)c * ld + rl] = rl < nrl ? Y[(size_t)(r0 + rl) * k + c] : 0.0;
+        Qs[(size_t)c * ld + rl] = (rl < nrl && r0 + rl == c) ? 1.0 : 0.0;
     }
     __syncthreads();
 
     // partial dots over the own rows >= j of column j (factor: x = column j;
     // Q: x = reflector j, 1 at row j) with the columns c >= j of `B`, stored
-    // as this CTA's partials P[par][c][cta]
+    // as this CTA's partials P[par][c][cta].  One thread per column sums its
+    // rows in order: a shuffle tree over 32 lanes spent 5 FP64 adds per lane
+    // on every column, more than the products themselves (nr ~ 54 rows)
     auto dots = [&](int j, int par, const double* B, bool reflector) {
         const int rl0 = max(0, j - r0);
-        const double* x = S + (size_t)j * nr;
-        for (int c = j + warp; c < k; c += nw) {
-            const double* a = B + (size_t)c * nr;
+        const double* x = S + (size_t)j * ld;
+        const bool one_at_j = reflector && j >= r0 && j < r1;  // the reflector's implicit 1 is a row of this CTA
+        for (int c = j + threadIdx.x; c < k; c += blockDim.x) {
+            const double* a = B + (size_t)c * ld;
             double p = 0.0;
-            for (int rl = rl0 + lane; rl < nrl; rl += 32)
-                p = fma((reflector && r0 + rl == j) ? 1.0 : x[rl], a[rl], p);
-            p = warp_sum(p);
-            if (lane == 0) P[((size_t)par * k + c) * G + cta] = p;
+            int rl = rl0;
+            if (one_at_j) p = a[rl++];
+            for (; rl < nrl; ++rl) p = fma(x[rl], a[rl], p);
+            P[((size_t)par * k + c) * G + cta] = p;
         }
     };
     // every CTA adds the G partials of each column c >= j in the same order:
@@ -289,7 +293,7 @@ __global__ void __launch_bounds__(PQR_THREADS) k_qr_persistent(const double* __r
     int step = 0;  // barriers passed: selects the buffers
     dots(0, 0, S, false);
     if (r0 == 0)
-        for (int c = threadIdx.x; c < k; c += blockDim.x) Ajg[c] = S[(size_t)c * nr];
+        for (int c = threadIdx.x; c < k; c += blockDim.x) Ajg[c] = S[(size_t)c * ld];
     for (int j = 0; j < k; ++j, ++step) {
         if (!grid_barrier(count, gen, G, err, limit)) return;
         read_totals(j, step);
@@ -308,17 +312,17 @@ __global__ void __launch_bounds__(PQR_THREADS) k_qr_persistent(const double* __r
         // column j becomes the reflector v (v_j = 1 implicit, beta on the diagonal)
         const int rl0 = max(0, j - r0);
         for (int rl = rl0 + threadIdx.x; rl < nrl; rl += blockDim.x)
-            S[(size_t)j * nr + rl] = (r0 + rl == j) ? bt : S[(size_t)j * nr + rl] * inv;
+            S[(size_t)j * ld + rl] = (r0 + rl == j) ? bt : S[(size_t)j * ld + rl] * inv;
         if (threadIdx.x == 0) {
             tau_s[j] = tu;
             beta_s[j] = bt;
         }
         __syncthreads();
         if (tu != 0.0) {
-            const double* v = S + (size_t)j * nr;
+            const double* v = S + (size_t)j * ld;
             for (int c = j + 1 + warp; c < k; c += nw) {
                 const double w = wv[c];
-                double* a = S + (size_t)c * nr;
+                double* a = S + (size_t)c * ld;
                 for (int rl = rl0 + lane; rl < nrl; rl += 32) a[rl] = fma(-w, (r0 + rl == j) ? 1.0 : v[rl], a[rl]);
             }
         }
@@ -327,7 +331,7 @@ __global__ void __launch_bounds__(PQR_THREADS) k_qr_persistent(const double* __r
             dots(j + 1, (step + 1) & 1, S, false);
             if (j + 1 >= r0 && j + 1 < r1)
                 for (int c = j + 1 + threadIdx.x; c < k; c += blockDim.x)
-                    Ajg[(size_t)((step + 1) & 1) * k + c] = S[(size_t)c * nr + (j + 1 - r0)];
+                    Ajg[(size_t)((step + 1) & 1) * k + c] = S[(size_t)c * ld + (j + 1 - r0)];
         }
     }
 
@@ -341,10 +345,10 @@ __global__ void __launch_bounds__(PQR_THREADS) k_qr_persistent(const double* __r
         read_totals(j, step);
         const double tu = tau_s[j];
         const int rl0 = max(0, j - r0);
-        const double* v = S + (size_t)j * nr;
+        const double* v = S + (size_t)j * ld;
         for (int c = j + warp; c < k; c += nw) {
             const double w = tu * tot[c];
-            double* q = Qs + (size_t)c * nr;
+            double* q = Qs + (size_t)c * ld;
             for (int rl = rl0 + lane; rl < nrl; rl += 32) q[rl] = fma(-w, (r0 + rl == j) ? 1.0 : v[rl], q[rl]);
         }
         __syncthreads();
@@ -358,7 +362,7 @@ __global__ void __launch_bounds__(PQR_THREADS) k_qr_persistent(const double* __r
     for (int t = threadIdx.x; t < nrl * k; t += blockDim.x) {
         const int rl = t / k, c = t - rl * k;
         const double sg = beta_s[c] < 0.0 ? -1.0 : 1.0;
-        Q[(size_t)(r0 + rl) * k + c] = sg * Qs[(size_t)c * nr + rl];
+        Q[(size_t)(r0 + rl) * k + c] = sg * Qs[(size_t)c * ld + rl];
     }
     for (int t = threadIdx.x; t < nrl * k; t += blockDim.x) {
         const int rl = t / k, c = t - rl * k, jr = r0 + rl;
@@ -366,7 +370,7 @@ __global__ void __launch_bounds__(PQR_THREADS) k_qr_persistent(const double* __r
         const double sg = beta_s[jr] < 0.0 ? -1.0 : 1.0;
         double v = 0.0;
         if (c == jr) v = fabs(beta_s[jr]);
-        else if (c > jr) v = sg * S[(size_t)c * nr + rl];
+        else if (c > jr) v = sg * S[(size_t)c * ld + rl];
         R[(size_t)jr * k + c] = v;
     }
 }
@@ -679,7 +683,7 @@ PqrPlan pqr_plan(int N, int k) {
         int g = std::min(std::min(nsm[dev], PQR_MAX_GRID), (N + PQR_MIN_ROWS - 1) / PQR_MIN_ROWS);
         if (g < 1) g = 1;
         const int nr = (N + g - 1) / g;
-        const size_t smem = sizeof(double) * (2 * (size_t)k * nr + 4 * (size_t)k);
+        const size_t smem = sizeof(double) * (2 * (size_t)k * (nr | 1) + 4 * (size_t)k);  // odd column stride
         if (smem > 200 * 1024) return p;
         p.grid = (N + nr - 1) / nr;
         p.nr = nr;
