@@ -4,6 +4,7 @@
 // transposed copy, so every reflector / rotation touches contiguous memory.
 // Each step is one launch; steps are ordered by the stream, so no kernel
 // waits on another.
+#include <cooperative_groups.h>
 #include <cuda_runtime.h>
 #include <algorithm>
 #include <cstdint>
@@ -399,7 +400,10 @@ __global__ void __launch_bounds__(256) k_jacobi_cluster(double* __restrict__ Gt,
     constexpr int RK = 8;  // cached entries per lane: k <= 32 RK
     const int b = blockIdx.x / csize, rank = blockIdx.x % csize;
     const int warps = blockDim.x >> 5, lane = threadIdx.x & 31;
-    const int gw = rank * warps + (threadIdx.x >> 5), nw = csize * warps;
+    // pairs dealt CTA-first (warp w of CTA r takes pairs w csize + r + ...):
+    // dealt warp-first the 72 pairs of k = 144 sat on 9 of the 16 SMs, whose
+    // FP64 pipes then set every round's length
+    const int gw = (threadIdx.x >> 5) * csize + rank, nw = csize * warps;
     double* g = Gt + (size_t)b * k * k;
     double* wm = Wt ? Wt + (size_t)b * k * k : nullptr;
     double* nb2 = nrm + (size_t)b * k;
@@ -447,8 +451,8 @@ __global__ void __launch_bounds__(256) k_jacobi_cluster(double* __restrict__ Gt,
                 for (int o = 16; o > 0; o >>= 1) c += __shfl_xor_sync(0xffffffffu, c, o);
                 if (a < 1e-280 || bb < 1e-280) continue;  // zero or near underflow: nothing to rotate
                 const double rel = fabs(c) / (sqrt(a) * sqrt(bb));
-                if (lane == 0) atomicMax(offb + sw, (unsigned long long)__double_as_longlong(rel));
                 if (!(rel > tol)) continue;
+                if (lane == 0) atomicMax(offb + sw, 1ull);  // this sweep rotated
                 const double z = (bb - a) / (2.0 * c);
                 const double t = (z >= 0.0 ? 1.0 : -1.0) / (fabs(z) + sqrt(1.0 + z * z));
                 const double cs = 1.0 / sqrt(1.0 + t * t), sn = cs * t;
@@ -501,12 +505,151 @@ __global__ void __launch_bounds__(256) k_jacobi_cluster(double* __restrict__ Gt,
             }
             cluster_sync();
         }
-        const double o = __longlong_as_double((long long)__ldcg(offb + sw));
+        const unsigned long long rotated = __ldcg(offb + sw);
         cluster_sync();  // everyone has read this sweep's value before anyone moves on
-        if (o < tol) break;
+        if (!rotated) break;
         // the last sweep still rotated: report that the cap was hit
         if (sw == max_sweeps - 1 && rank == 0 && threadIdx.x == 0 && status) atomicExch(status, 1);
     }
+}
+
+// ---------------------------------------------------------------------------
+// The same one-sided Jacobi with the matrix in the cluster's distributed
+// shared memory: column c of G^T (and of W^T) lives in CTA c % csize, slot
+// c / csize, with its squared norm beside it.  The warp that rotates a pair
+// reads and writes both columns in their owners' shared memory, so a
+// round's data never leaves the cluster and its release/acquire barrier
+// orders shared-memory traffic only (through L2 every round had to wait for
+// its global stores).  Rounds, pairs, tolerance and the per-sweep status
+// are those of k_jacobi_cluster; G^T and W^T are copied in at the start and
+// out at the end.  Every thread runs every barrier, and after the last
+// barrier a CTA touches only its own shared memory.
+// ---------------------------------------------------------------------------
+__global__ void __launch_bounds__(256) k_jacobi_dsmem(double* __restrict__ Gt, double* __restrict__ Wt, int k, int n,
+                                                     int max_sweeps, double tol,
+                                                     unsigned long long* __restrict__ off, int* __restrict__ status) {
+    namespace cg = cooperative_groups;
+    extern __shared__ double jsm[];
+    cg::cluster_group cl = cg::this_cluster();
+    const int csize = (int)cl.num_blocks(), rank = (int)cl.block_rank();
+    const int b = blockIdx.x / csize;
+    const int slots = (k + csize - 1) / csize;
+    const int warps = blockDim.x >> 5, lane = threadIdx.x & 31;
+    // pairs dealt CTA-first (warp w of CTA r takes pairs w csize + r + ...):
+    // dealt warp-first the 72 pairs of k = 144 sat on 9 of the 16 SMs, whose
+    // FP64 pipes then set every round's length
+    const int gw = (threadIdx.x >> 5) * csize + rank, nw = csize * warps;
+    double* gs = jsm;                               // [slots][k]
+    double* ws = gs + (size_t)slots * k;            // [slots][k], when W is accumulated
+    double* ns = ws + (size_t)slots * k;            // [slots] squared column norms
+    double* g = Gt + (size_t)b * k * k;
+    double* wm = Wt ? Wt + (size_t)b * k * k : nullptr;
+    unsigned long long* offb = off + (size_t)b * max_sweeps;
+    for (int t = threadIdx.x; t < slots * k; t += blockDim.x) {
+        const int sl = t / k, i = t - sl * k, c = sl * csize + rank;
+        gs[t] = c < k ? g[(size_t)c * k + i] : 0.0;
+        if (wm) ws[t] = c < k ? wm[(size_t)c * k + i] : 0.0;
+    }
+    cluster_sync();
+    auto gcol = [&](int c) { return cl.map_shared_rank(gs + (size_t)(c / csize) * k, c % csize); };
+    auto wcol = [&](int c) { return cl.map_shared_rank(ws + (size_t)(c / csize) * k, c % csize); };
+    auto ncol = [&](int c) { return cl.map_shared_rank(ns + c / csize, c % csize); };
+    constexpr int RK = 8;  // cached entries per lane: k <= 32 RK
+    const bool cached = k <= 32 * RK;
+    for (int sw = 0; sw < max_sweeps; ++sw) {
+        // exact squared norms of the own columns at the start of every sweep
+        for (int sl = threadIdx.x >> 5; sl < slots; sl += warps) {
+            const double* x = gs + (size_t)sl * k;
+            double a = 0.0;
+            for (int i = lane; i < k; i += 32) a = fma(x[i], x[i], a);
+            for (int o = 16; o > 0; o >>= 1) a += __shfl_xor_sync(0xffffffffu, a, o);
+            if (lane == 0) ns[sl] = a;
+        }
+        cluster_sync();
+        for (int r = 0; r < n - 1; ++r) {
+            for (int p = gw; p < n / 2; p += nw) {
+                auto pos = [&](int i) { return i == 0 ? 0 : 1 + (i - 1 + r) % (n - 1); };
+                int P = pos(p), Q = pos(n - 1 - p);
+                if (P >= k || Q >= k) continue;
+                if (P > Q) { const int t = P; P = Q; Q = t; }
+                double* gp = gcol(P);
+                double* gq = gcol(Q);
+                double* np = ncol(P);
+                double* nq = ncol(Q);
+                const double a = *np, bb = *nq;
+                double xr[RK], yr[RK];
+                double c = 0.0;
+                if (cached) {
+#pragma unroll
+                    for (int u = 0; u < RK; ++u) {
+                        const int i = lane + 32 * u;
+                        xr[u] = i < k ? gp[i] : 0.0;
+                        yr[u] = i < k ? gq[i] : 0.0;
+                    }
+#pragma unroll
+                    for (int u = 0; u < RK; ++u) c = fma(xr[u], yr[u], c);
+                } else {
+                    for (int i = lane; i < k; i += 32) c = fma(gp[i], gq[i], c);
+                }
+                for (int o = 16; o > 0; o >>= 1) c += __shfl_xor_sync(0xffffffffu, c, o);
+                if (a < 1e-280 || bb < 1e-280) continue;  // zero or near underflow: nothing to rotate
+                const double rel = fabs(c) / (sqrt(a) * sqrt(bb));
+                if (!(rel > tol)) continue;
+                if (lane == 0) atomicMax(offb + sw, 1ull);  // this sweep rotated
+                const double z = (bb - a) / (2.0 * c);
+                const double t = (z >= 0.0 ? 1.0 : -1.0) / (fabs(z) + sqrt(1.0 + z * z));
+                const double cs = 1.0 / sqrt(1.0 + t * t), sn = cs * t;
+                if (cached) {
+#pragma unroll
+                    for (int u = 0; u < RK; ++u) {
+                        const int i = lane + 32 * u;
+                        if (i < k) {
+                            gp[i] = cs * xr[u] - sn * yr[u];
+                            gq[i] = sn * xr[u] + cs * yr[u];
+                        }
+                    }
+                } else {
+                    for (int i = lane; i < k; i += 32) {
+                        const double x = gp[i], y = gq[i];
+                        gp[i] = cs * x - sn * y;
+                        gq[i] = sn * x + cs * y;
+                    }
+                }
+                if (lane == 0) {
+                    *np = a - t * c;
+                    *nq = bb + t * c;
+                }
+                if (wm) {
+                    double* wp = wcol(P);
+                    double* wq = wcol(Q);
+                    for (int i = lane; i < k; i += 32) {
+                        const double x = wp[i], y = wq[i];
+                        wp[i] = cs * x - sn * y;
+                        wq[i] = sn * x + cs * y;
+                    }
+                }
+            }
+            cluster_sync();
+        }
+        const unsigned long long rotated = __ldcg(offb + sw);
+        cluster_sync();  // everyone has read this sweep's value before anyone moves on
+        if (!rotated) break;
+        if (sw == max_sweeps - 1 && rank == 0 && threadIdx.x == 0 && status) atomicExch(status, 1);
+    }
+    // own columns back to global memory
+    for (int t = threadIdx.x; t < slots * k; t += blockDim.x) {
+        const int sl = t / k, i = t - sl * k, c = sl * csize + rank;
+        if (c < k) {
+            g[(size_t)c * k + i] = gs[t];
+            if (wm) wm[(size_t)c * k + i] = ws[t];
+        }
+    }
+}
+
+constexpr size_t JACOBI_DSMEM_MAX = 200 * 1024;
+inline size_t jacobi_dsmem_bytes(int k, int csize) {
+    const size_t slots = (size_t)(k + csize - 1) / csize;
+    return sizeof(double) * (2 * slots * k + slots);
 }
 
 inline unsigned grid_for(size_t n, unsigned threads = 256) {
@@ -808,14 +951,56 @@ int jacobi_cluster_size() {
 // Jacobi on nb matrices: one cluster per matrix when the device allows it,
 // else one launch per round.  *status (optional) becomes 1 when a matrix
 // still needed rotations in the last allowed sweep.
+// Whether the shared-memory Jacobi can run with `bytes` of shared memory per
+// CTA in a cluster of csize on the current device (attributes set once per
+// device; occupancy queries launch nothing).
+bool jacobi_dsmem_ok(size_t bytes, int csize) {
+    static std::mutex mu;
+    static unsigned long long attr_set = 0;
+    if (bytes > JACOBI_DSMEM_MAX) return false;
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) return false;
+    {
+        std::lock_guard<std::mutex> lock(mu);
+        if (!(attr_set >> dev & 1ull)) {
+            if (cudaFuncSetAttribute(k_jacobi_dsmem, cudaFuncAttributeNonPortableClusterSizeAllowed, 1) != cudaSuccess ||
+                cudaFuncSetAttribute(k_jacobi_dsmem, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                     (int)JACOBI_DSMEM_MAX) != cudaSuccess) {
+                cudaGetLastError();
+                return false;
+            }
+            attr_set |= 1ull << dev;
+        }
+    }
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3((unsigned)csize, 1, 1);
+    cfg.blockDim = dim3(256, 1, 1);
+    cfg.dynamicSmemBytes = bytes;
+    cudaLaunchAttribute at[1];
+    at[0].id = cudaLaunchAttributeClusterDimension;
+    at[0].val.clusterDim.x = csize;
+    at[0].val.clusterDim.y = 1;
+    at[0].val.clusterDim.z = 1;
+    cfg.attrs = at;
+    cfg.numAttrs = 1;
+    int nclusters = 0;
+    if (cudaOccupancyMaxActiveClusters(&nclusters, k_jacobi_dsmem, &cfg) != cudaSuccess) {
+        cudaGetLastError();
+        return false;
+    }
+    return nclusters > 0;
+}
+
 cudaError_t jacobi(double* Gt, double* Wt, int k, int n, int nb, unsigned long long* off, double* nrm,
                    int* status, cudaStream_t s) {
     const int csize = jacobi_cluster_size();
     if (csize > 0) {
+        const size_t dsm = jacobi_dsmem_bytes(k, csize);
+        const bool in_smem = jacobi_dsmem_ok(dsm, csize);
         cudaLaunchConfig_t cfg = {};
         cfg.gridDim = dim3((unsigned)(nb * csize), 1, 1);
         cfg.blockDim = dim3(256, 1, 1);
-        cfg.dynamicSmemBytes = 0;
+        cfg.dynamicSmemBytes = in_smem ? dsm : 0;
         cfg.stream = s;
         cudaLaunchAttribute at[1];
         at[0].id = cudaLaunchAttributeClusterDimension;
@@ -825,6 +1010,9 @@ cudaError_t jacobi(double* Gt, double* Wt, int k, int n, int nb, unsigned long l
         cfg.attrs = at;
         cfg.numAttrs = 1;
         ++g_launches;
+        if (in_smem)
+            return cudaLaunchKernelEx(&cfg, k_jacobi_dsmem, Gt, Wt, k, n, JACOBI_MAX_SWEEPS, jacobi_tol(k), off,
+                                      status);
         return cudaLaunchKernelEx(&cfg, k_jacobi_cluster, Gt, Wt, k, n, JACOBI_MAX_SWEEPS, jacobi_tol(k), off, nrm,
                                   csize, status);
     }
@@ -841,7 +1029,8 @@ cudaError_t jacobi(double* Gt, double* Wt, int k, int n, int nb, unsigned long l
 }
 
 // scratch: status word (256 bytes), G^T and W^T (k x k each), squared column
-// norms (k), per-sweep off-diagonal maxima
+// norms (k), per-sweep words (the cluster kernels' "rotated" flags, the
+// per-round kernels' off-diagonal maxima)
 constexpr size_t svd_ws_bytes_c(int k) {
     return 256 + sizeof(double) * (2 * (size_t)k * k + k) + sizeof(unsigned long long) * JACOBI_MAX_SWEEPS + 256;
 }
@@ -1068,7 +1257,7 @@ cudaError_t small_eig(const double* H, int m, int ldh, double period, double* ou
 }
 
 // Two independent SVDs in one Jacobi launch (two clusters); the layout of
-// svd() per matrix: status word, then G^T, W^T, norms, off-diagonal maxima
+// svd() per matrix: status word, then G^T, W^T, norms, per-sweep words
 size_t svd2_ws_bytes(int k) {
     return 256 + sizeof(double) * 2 * (2 * (size_t)k * k + k) + sizeof(unsigned long long) * 2 * JACOBI_MAX_SWEEPS +
            256;
