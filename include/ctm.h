@@ -384,18 +384,20 @@ ctm_status ctm_correlation(ctm_handle h, const double* opA, const double* opB, i
  * -log(lambda_1 / lambda_0), with e_2, e_3, ... for the finite-chi
  * extrapolation 1/xi(inf) = 1/xi(chi) + k (e_2 - e_1)).  dir 0: the two
  * columns of row y = index, acting along +x; dir 1: the two rows of column
- * x = index, acting along +y.  Block subspace iteration with `block`
- * orthonormal vectors (nev <= block <= 32, block <= chi^2 D^2; block >= nev
- * + 2 converges faster) and a Rayleigh-Ritz step per iteration, until the
- * first nev ratios lambda_i / lambda_0 change by less than tol in one
- * iteration or max_iter iterations are done (then CTM_NOT_CONVERGED).
+ * x = index, acting along +y.  Explicitly restarted block Arnoldi: each
+ * cycle builds an orthonormal basis of the block Krylov space of `block`
+ * vectors and p = min(32 / block, chi^2 D^2 / block) >= 2 powers of the
+ * transfer matrix (nev <= block <= 16), takes the eigenvalues of its
+ * Rayleigh-Ritz matrix, and restarts from the leading Ritz vectors, until
+ * the first nev moduli |lambda_i / lambda_0| change by less than tol in one
+ * cycle or max_iter cycles are done (then CTM_NOT_CONVERGED).
  * out_host: 4 nev doubles -- Re(lambda_i / lambda_0), Im(lambda_i /
  * lambda_0), |lambda_i|, e_i = -ln|lambda_i / lambda_0| / 2 per lattice
  * spacing (the period is 2 sites; +inf for lambda_i = 0) -- for i < nev
  * with |lambda_i| descending; the correlation length is 1 / e_1.  *iters,
- * *change (optional): iterations done and the last change.  Each iteration
- * costs 2 block column contractions.  Allocates 4 block chi^2 D^2 doubles
- * plus a QR workspace per call.  Synchronises. */
+ * *change (optional): cycles done and the last change.  Each cycle costs
+ * 2 block p column contractions.  Allocates (block p + 3 block) chi^2 D^2
+ * doubles plus a QR workspace per call.  Synchronises. */
 ctm_status ctm_transfer_spectrum(ctm_handle h, int dir, int index, int nev, int block, int max_iter, double tol,
                                  double* out_host, int* iters, double* change);
 

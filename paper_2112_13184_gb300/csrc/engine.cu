@@ -1179,8 +1179,15 @@ ctm_status correlation(ctm_ctx* h, const double* opA_h, const double* opB_h, int
 }
 
 // Leading eigenvalues of the period transfer matrix of row `index` of frame
-// m: block subspace iteration V <- orth(T V) with Rayleigh-Ritz on
-// H = V (T V)^T; V holds `blk` orthonormal vectors as rows (blk x n).
+// m: explicitly restarted block Arnoldi.  A cycle builds an orthonormal
+// basis Q of the block Krylov space {V, T V, ..., T^(p-1) V} (blocks of
+// `blk` vectors as rows, m = blk p <= 32) by block Gram-Schmidt (two passes,
+// and the new block orthogonalised once more after its QR, so that a
+// breakdown -- a residual at rounding level -- still yields an orthonormal
+// block), with H = Q^T T Q assembled from the projection coefficients; the
+// eigenvalues of H (Rayleigh-Ritz) are the estimates, and the next cycle
+// restarts from the real parts of the leading Ritz vectors.  (Subspace
+// iteration, tried first, needed ~4x the products on clustered spectra.)
 ctm_status transfer_spectrum(ctm_ctx* h, int dir, int index, int nev, int blk, int max_iter, double tol,
                              double* out, int* iters, double* change) {
     CKS(check_ready(h));
@@ -1191,74 +1198,115 @@ ctm_status transfer_spectrum(ctm_ctx* h, int dir, int index, int nev, int blk, i
     frame_pos(m, dir == 0 ? index * 2 : index, &xs, &ys);  // site (0, index) or (index, 0)
     const int s0 = FM.site(m, 0, ys), s1 = FM.site(m, 1, ys);
     const size_t n = (size_t)h->chi * h->N;
-    double *V = nullptr, *W = nullptr, *Y = nullptr, *Q = nullptr, *Rr = nullptr, *H = nullptr, *ev = nullptr;
+    const int p = std::min(ctm::small_eig_max() / blk, (int)(n / blk));  // Krylov blocks per cycle
+    const int mk = blk * p;                                              // basis size
+    if (p < 2) {
+        h->err = "transfer spectrum: block too large for a Krylov space of two blocks";
+        return CTM_ERR_ARG;
+    }
+    double *Qa = nullptr, *W = nullptr, *Y = nullptr, *Qn = nullptr, *Rr = nullptr, *Cc = nullptr, *H = nullptr;
+    double *ev = nullptr, *evr = nullptr, *Yr = nullptr;
     void* qws = nullptr;
     int* est = nullptr;
     ctm_status st = CTM_OK;
     auto body = [&]() -> ctm_status {
-        CKS(allocd_tmp(h, &V, (size_t)blk * n));
+        CKS(allocd_tmp(h, &Qa, (size_t)mk * n));
         CKS(allocd_tmp(h, &W, (size_t)blk * n));
         CKS(allocd_tmp(h, &Y, (size_t)blk * n));
-        CKS(allocd_tmp(h, &Q, (size_t)blk * n));
+        CKS(allocd_tmp(h, &Qn, (size_t)blk * n));
         CKS(allocd_tmp(h, &Rr, (size_t)blk * blk));
-        CKS(allocd_tmp(h, &H, (size_t)blk * blk));
-        CKS(allocd_tmp(h, &ev, (size_t)4 * blk + 8));
+        CKS(allocd_tmp(h, &Cc, (size_t)mk * blk));
+        CKS(allocd_tmp(h, &H, (size_t)mk * mk));
+        CKS(allocd_tmp(h, &ev, (size_t)4 * mk + 8));
+        CKS(allocd_tmp(h, &evr, (size_t)2 * mk));
+        CKS(allocd_tmp(h, &Yr, (size_t)blk * mk));
         if (cudaMalloc(&qws, ctm::qr_ws_bytes((int)n, blk)) != cudaSuccess) {
+            cudaGetLastError();
             h->err = "transfer spectrum: out of device memory";
             return CTM_ERR_OOM;
         }
-        est = (int*)(ev + 4 * blk);
+        est = (int*)(ev + 4 * mk);
         double *tmp = b.v[4], *t3p = b.v[6], *mid = b.v[7];
-        auto orth = [&](const double* src) -> ctm_status {  // V = rows of an orthonormal basis of src's rows
-            CKS(perm(h, src, Y, {blk, (int)n}, {1, 0}));
-            CK(ctm::qr(Y, (int)n, blk, Q, Rr, qws, h->stream, h->flag + 1));
-            return perm(h, Q, V, {(int)n, blk}, {1, 0});
+        const int nn = (int)n;
+        // rows of dst (blk x n) = an orthonormal basis of the rows of src
+        auto orth = [&](const double* src, double* dst) -> ctm_status {
+            CKS(perm(h, src, Y, {blk, nn}, {1, 0}));
+            CK(ctm::qr(Y, nn, blk, Qn, Rr, qws, h->stream, h->flag + 1));
+            return perm(h, Qn, dst, {nn, blk}, {1, 0});
+        };
+        // W -= (Qa[0:L] W^T)^T Qa[0:L], the coefficients into Cc (L x blk); twice
+        auto project = [&](int L, double* Hcol) -> ctm_status {
+            for (int pass = 0; pass < 2; ++pass) {
+                CK(ctm::dgemm(false, true, L, blk, nn, 1.0, Qa, nn, W, nn, 0.0, Cc, blk, h->stream, h->splitk,
+                              h->splitk_n));
+                CK(ctm::dgemm(true, false, blk, nn, L, -1.0, Cc, blk, Qa, nn, 1.0, W, nn, h->stream, nullptr, 0));
+                if (Hcol) CK(ctm::add_block(Cc, L, blk, blk, Hcol, mk, h->stream));
+            }
+            return CTM_OK;
         };
         CK(ctm::rng_normal(W, (size_t)blk * n, h->opt.seed, 0x5452414eull + h->rng_counter++, h->stream));
-        CKS(orth(W));
-        std::vector<double> prev(2 * nev, 0.0), cur(4 * blk);
+        CKS(orth(W, Qa));
+        std::vector<double> prev(nev, -1.0), cur(4 * mk);
         double delta = INFINITY;
         int it = 0;
         st = CTM_NOT_CONVERGED;
         for (it = 1; it <= max_iter; ++it) {
-            for (int j = 0; j < blk; ++j) {
-                CKS(strip_column(h, m, s0, V + (size_t)j * n, h->Alu[s0][m & 3], mid, t3p, tmp));
-                CKS(strip_column(h, m, s1, mid, h->Alu[s1][m & 3], W + (size_t)j * n, t3p, tmp));
+            CK(cudaMemsetAsync(H, 0, sizeof(double) * mk * mk, h->stream));
+            for (int sb = 0; sb < p; ++sb) {
+                for (int j = 0; j < blk; ++j) {
+                    const double* v = Qa + ((size_t)sb * blk + j) * n;
+                    CKS(strip_column(h, m, s0, v, h->Alu[s0][m & 3], mid, t3p, tmp));
+                    CKS(strip_column(h, m, s1, mid, h->Alu[s1][m & 3], W + (size_t)j * n, t3p, tmp));
+                }
+                const int L = (sb + 1) * blk;
+                CKS(project(L, H + (size_t)sb * blk));
+                if (sb + 1 < p) {
+                    // W = Q_new R: R is the subdiagonal block of H
+                    CKS(perm(h, W, Y, {blk, nn}, {1, 0}));
+                    CK(ctm::qr(Y, nn, blk, Qn, Rr, qws, h->stream, h->flag + 1));
+                    CK(ctm::add_block(Rr, blk, blk, blk, H + (size_t)L * mk + (size_t)sb * blk, mk, h->stream));
+                    CKS(perm(h, Qn, W, {nn, blk}, {1, 0}));
+                    CKS(project(L, nullptr));       // the new block once more against the basis
+                    CKS(orth(W, Qa + (size_t)L * n));
+                }
             }
-            // H[i][j] = v_i . (T v_j)
-            CK(ctm::dgemm(false, true, blk, blk, (int)n, 1.0, V, (int)n, W, (int)n, 0.0, H, blk, h->stream,
-                          h->splitk, h->splitk_n));
-            CK(ctm::small_eig(H, blk, blk, 2.0, ev, est, h->stream));
-            CK(cudaMemcpyAsync(cur.data(), ev, sizeof(double) * 4 * blk, cudaMemcpyDeviceToHost, h->stream));
+            CK(ctm::small_eig(H, mk, mk, 2.0, ev, est, h->stream, evr));
+            CK(cudaMemcpyAsync(cur.data(), ev, sizeof(double) * 4 * mk, cudaMemcpyDeviceToHost, h->stream));
             CK(cudaStreamSynchronize(h->stream));
+            // change of the moduli |lambda_i / lambda_0| (what e_i and xi are
+            // made of): among eigenvalues of equal modulus -- a complex pair,
+            // or +-lambda -- the order, and so the complex ratio, may swap
+            // from one cycle to the next
             delta = 0.0;
             for (int i = 0; i < nev; ++i) {
-                delta = std::max(delta, std::fabs(cur[i] - prev[2 * i]));
-                delta = std::max(delta, std::fabs(cur[blk + i] - prev[2 * i + 1]));
-                prev[2 * i] = cur[i];
-                prev[2 * i + 1] = cur[blk + i];
+                const double mod = std::hypot(cur[i], cur[mk + i]);
+                delta = std::max(delta, std::fabs(mod - prev[i]));
+                prev[i] = mod;
             }
             if (!(delta == delta)) delta = INFINITY;
-            CKS(orth(W));
             if (delta < tol) {
                 st = CTM_OK;
                 break;
             }
+            // restart: V = orth(Y_ritz Q), Y_ritz the real basis of the leading Ritz vectors
+            CK(ctm::ritz_basis(H, mk, mk, evr, blk, Yr, h->stream));
+            CK(ctm::dgemm(false, false, blk, nn, mk, 1.0, Yr, mk, Qa, nn, 0.0, W, nn, h->stream, nullptr, 0));
+            CKS(orth(W, Qa));
         }
         CKS(read_flag(h));
         if (iters) *iters = std::min(it, max_iter);
         if (change) *change = delta;
         for (int i = 0; i < nev; ++i) {
             out[i] = cur[i];
-            out[nev + i] = cur[blk + i];
-            out[2 * nev + i] = cur[2 * blk + i];
-            out[3 * nev + i] = cur[3 * blk + i];
+            out[nev + i] = cur[mk + i];
+            out[2 * nev + i] = cur[2 * mk + i];
+            out[3 * nev + i] = cur[3 * mk + i];
         }
         return st;
     };
     st = body();
     cudaStreamSynchronize(h->stream);
-    for (double* p : {V, W, Y, Q, Rr, H, ev}) cudaFree(p);
+    for (double* q : {Qa, W, Y, Qn, Rr, Cc, H, ev, evr, Yr}) cudaFree(q);
     cudaFree(qws);
     return st;
 }

@@ -26,6 +26,8 @@ cudaError_t permute(const double* src, double* dst, int ndim, const int* dims, c
                     cudaStream_t s);
 // X[r*ld + c] *= w[c], r < rows, c < cols
 cudaError_t scale_cols(double* X, int rows, int cols, int ld, const double* w, cudaStream_t s);
+// dst[i][j] += src[i][j], i < rows, j < cols (row strides lds, ldd)
+cudaError_t add_block(const double* src, int rows, int cols, int lds, double* dst, int ldd, cudaStream_t s);
 // w[j] = s[j] > cut*s[0] ? 1/sqrt(s[j]) : 0
 cudaError_t inv_sqrt_cut(const double* sv, double* w, int n, double cut, cudaStream_t s);
 // bits of max|x| into *maxbits (must be zeroed first); sticky
@@ -70,7 +72,13 @@ cudaError_t svd_noalloc(const double* G, int k, double* U, double* S, double* V,
 // sorted by |l_i| descending; *status (optional) 0, 1 = QR iteration cap hit,
 // 2 = all eigenvalues zero
 int small_eig_max();
-cudaError_t small_eig(const double* H, int m, int ldh, double period, double* out, int* status, cudaStream_t s);
+cudaError_t small_eig(const double* H, int m, int ldh, double period, double* out, int* status, cudaStream_t s,
+                      double* ev = nullptr);
+// real basis of the Ritz vectors of the leading eigenvalues of H (m x m,
+// row stride ldh): ev = small_eig's sorted eigenvalues (re, im pairs);
+// Y[j][0..m) for j < nvec holds Re y_i of a real eigenvalue, or Re y_i and
+// Im y_i of a complex pair (its conjugate skipped), y_i by inverse iteration
+cudaError_t ritz_basis(const double* H, int m, int ldh, const double* ev, int nvec, double* Y, cudaStream_t s);
 // singular values only (descending) of a batch of nb k x k matrices, each
 // normalised to sum 1; Gs contiguous, out nb*k
 size_t svals_ws_bytes(int k, int nb);

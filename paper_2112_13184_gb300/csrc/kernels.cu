@@ -343,7 +343,23 @@ inline unsigned grid_for(size_t n, unsigned threads = 256) {
     if (b == 0) b = 1;
     return (unsigned)b;
 }
+// dst[i][j] += src[i][j] for a rows x cols block (row strides lds, ldd)
+__global__ void k_add_block(const double* __restrict__ src, int rows, int cols, int lds, double* __restrict__ dst,
+                            int ldd) {
+    const size_t total = (size_t)rows * cols;
+    for (size_t t = blockIdx.x * (size_t)blockDim.x + threadIdx.x; t < total; t += (size_t)gridDim.x * blockDim.x) {
+        const int i = (int)(t / cols), j = (int)(t % cols);
+        dst[(size_t)i * ldd + j] += src[(size_t)i * lds + j];
+    }
+}
 }  // namespace
+
+cudaError_t add_block(const double* src, int rows, int cols, int lds, double* dst, int ldd, cudaStream_t s) {
+    if (rows <= 0 || cols <= 0) return cudaSuccess;
+    ++g_launches;
+    k_add_block<<<grid_for((size_t)rows * cols), 256, 0, s>>>(src, rows, cols, lds, dst, ldd);
+    return cudaGetLastError();
+}
 
 cudaError_t scale_cols(double* X, int rows, int cols, int ld, const double* w, cudaStream_t s) {
     if (rows <= 0 || cols <= 0) return cudaSuccess;

@@ -1103,7 +1103,7 @@ __device__ __forceinline__ cd c_sqrt(cd z) {
 constexpr int SMALL_EIG_MAX = 32;
 
 __global__ void k_small_eig(const double* __restrict__ H, int m, int ldh, double period, double* __restrict__ out,
-                            int* __restrict__ status) {
+                            int* __restrict__ status, double* __restrict__ evout) {
     __shared__ double R[SMALL_EIG_MAX][SMALL_EIG_MAX];
     __shared__ cd Z[SMALL_EIG_MAX][SMALL_EIG_MAX];
     __shared__ cd ev[SMALL_EIG_MAX];
@@ -1242,17 +1242,96 @@ __global__ void k_small_eig(const double* __restrict__ H, int m, int ldh, double
         out[m + i] = r.im;
         out[2 * m + i] = ai;
         out[3 * m + i] = (a0 > 0.0 && ai > 0.0) ? -log(ai / a0) / period : INFINITY;
+        if (evout) {
+            evout[2 * i] = ev[i].re;
+            evout[2 * i + 1] = ev[i].im;
+        }
     }
     if (status) *status = st;
+}
+
+// Ritz vectors of the leading eigenvalues by inverse iteration on the small
+// matrix: (H - mu I) y = y_prev with mu = lambda (1 + 1e-10), three solves
+// after one LU factorisation with partial pivoting (complex), y normalised.
+// A real eigenvalue gives Re y; a complex pair gives Re y and Im y (the
+// conjugate's eigenvector adds nothing real).  One thread.
+__global__ void k_ritz_basis(const double* __restrict__ H, int m, int ldh, const double* __restrict__ ev, int nvec,
+                             double* __restrict__ Y) {
+    __shared__ cd L[SMALL_EIG_MAX][SMALL_EIG_MAX];
+    __shared__ cd y[SMALL_EIG_MAX];
+    __shared__ int piv[SMALL_EIG_MAX];
+    if (threadIdx.x != 0 || blockIdx.x != 0) return;
+    const double scale = hypot(ev[0], ev[1]);
+    const double tiny = (scale > 0.0 ? scale : 1.0) * 1e-300;
+    int out = 0;
+    for (int i = 0; i < m && out < nvec; ++i) {
+        const cd lam = c_mk(ev[2 * i], ev[2 * i + 1]);
+        const cd mu = c_add(lam, c_scale(lam, 1e-10));
+        for (int r = 0; r < m; ++r)
+            for (int c = 0; c < m; ++c) L[r][c] = c_mk(H[(size_t)r * ldh + c] - (r == c ? mu.re : 0.0), r == c ? -mu.im : 0.0);
+        // LU with partial pivoting, in place
+        for (int c = 0; c < m; ++c) {
+            int p = c;
+            double best = c_abs(L[c][c]);
+            for (int r = c + 1; r < m; ++r)
+                if (c_abs(L[r][c]) > best) { best = c_abs(L[r][c]); p = r; }
+            piv[c] = p;
+            if (p != c)
+                for (int q = 0; q < m; ++q) { const cd t = L[c][q]; L[c][q] = L[p][q]; L[p][q] = t; }
+            if (c_abs(L[c][c]) < tiny) L[c][c] = c_mk(tiny, 0.0);
+            for (int r = c + 1; r < m; ++r) {
+                const cd f = c_div(L[r][c], L[c][c]);
+                L[r][c] = f;
+                for (int q = c + 1; q < m; ++q) L[r][q] = c_sub(L[r][q], c_mul(f, L[c][q]));
+            }
+        }
+        for (int r = 0; r < m; ++r) y[r] = c_mk(1.0, 0.0);
+        for (int it = 0; it < 3; ++it) {
+            for (int c = 0; c < m; ++c)  // row interchanges, then L (unit lower) forward
+                if (piv[c] != c) { const cd t = y[c]; y[c] = y[piv[c]]; y[piv[c]] = t; }
+            for (int r = 0; r < m; ++r)
+                for (int c = 0; c < r; ++c) y[r] = c_sub(y[r], c_mul(L[r][c], y[c]));
+            for (int r = m - 1; r >= 0; --r) {  // U backward
+                for (int c = r + 1; c < m; ++c) y[r] = c_sub(y[r], c_mul(L[r][c], y[c]));
+                y[r] = c_div(y[r], L[r][r]);
+            }
+            double nrm = 0.0;
+            for (int r = 0; r < m; ++r) nrm = hypot(nrm, c_abs(y[r]));
+            const double inv = nrm > 0.0 ? 1.0 / nrm : 0.0;
+            for (int r = 0; r < m; ++r) y[r] = c_scale(y[r], inv);
+        }
+        for (int r = 0; r < m; ++r) Y[(size_t)out * m + r] = y[r].re;
+        ++out;
+        const bool pair = fabs(lam.im) > 1e-12 * (scale > 0.0 ? scale : 1.0);
+        if (pair) {
+            if (out < nvec) {
+                for (int r = 0; r < m; ++r) Y[(size_t)out * m + r] = y[r].im;
+                ++out;
+            }
+            if (i + 1 < m && fabs(ev[2 * (i + 1)] - lam.re) <= 1e-9 * scale &&
+                fabs(ev[2 * (i + 1) + 1] + lam.im) <= 1e-9 * scale)
+                ++i;  // skip the conjugate
+        }
+    }
+    for (; out < nvec; ++out)  // fewer eigenvalues than vectors asked for
+        for (int r = 0; r < m; ++r) Y[(size_t)out * m + r] = (r == out) ? 1.0 : 0.0;
 }
 }  // namespace
 
 int small_eig_max() { return SMALL_EIG_MAX; }
 
-cudaError_t small_eig(const double* H, int m, int ldh, double period, double* out, int* status, cudaStream_t s) {
+cudaError_t small_eig(const double* H, int m, int ldh, double period, double* out, int* status, cudaStream_t s,
+                      double* ev) {
     if (m < 1 || m > SMALL_EIG_MAX || ldh < m || !H || !out || !(period > 0.0)) return cudaErrorInvalidValue;
     ++g_launches;
-    k_small_eig<<<1, 32, 0, s>>>(H, m, ldh, period, out, status);
+    k_small_eig<<<1, 32, 0, s>>>(H, m, ldh, period, out, status, ev);
+    return cudaGetLastError();
+}
+
+cudaError_t ritz_basis(const double* H, int m, int ldh, const double* ev, int nvec, double* Y, cudaStream_t s) {
+    if (m < 1 || m > SMALL_EIG_MAX || ldh < m || nvec < 1 || nvec > m || !H || !ev || !Y) return cudaErrorInvalidValue;
+    ++g_launches;
+    k_ritz_basis<<<1, 32, 0, s>>>(H, m, ldh, ev, nvec, Y);
     return cudaGetLastError();
 }
 
