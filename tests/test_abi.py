@@ -74,3 +74,49 @@ def test_op_from_elements_matches_oracle_and_golden():
     np.testing.assert_array_equal(op, np.kron(o["Sp"], o["Sm"]))
     with pytest.raises(ctm.CtmError):
         ctm.ctm_op_from_elements(2, 2, [(2, 0, 0, 0, 1.0, 0.0)])
+
+
+def test_footprint_follows_batched_cuts_and_scheme():
+    """Host arithmetic of ctm_footprint_bytes: batch_cuts keeps a second
+    cut's four N x N corners (and, in a tensor-core mode, their eight slice
+    caches) resident; the schemes' slice caches order FP64 < 3xTF32 (2 FP32
+    slices) ~ split-BF16 (3 BF16 slices) < emulated FP64 with 5 BF16 slices."""
+    from paper_2112_13184_gb300 import ctm
+    d, D, chi = 3, 8, 64
+    N = chi * D * D
+
+    def fp(prec, batch):
+        return ctm.ctm_footprint_bytes(d, D, ctm.ctm_default_options(chi=chi, precision=prec, batch_cuts=batch))
+
+    assert fp(ctm.CTM_FP64, 1) - fp(ctm.CTM_FP64, 0) >= 4 * N * N * 8
+    # eight more slice caches of 5 BF16 slices of an N x N corner
+    assert fp(ctm.CTM_OZAKI_BF16, 1) - fp(ctm.CTM_OZAKI_BF16, 0) >= 4 * N * N * 8 + 8 * 5 * N * N * 2
+    f64, tf32, bf3, oz5 = (fp(p, 1) for p in (ctm.CTM_FP64, ctm.CTM_3XTF32, ctm.CTM_SPLIT_BF16, ctm.CTM_OZAKI_BF16))
+    assert f64 < bf3 < oz5 and f64 < tf32 < oz5
+
+
+def test_unbuilt_scheme_and_bad_arena_are_rejected_without_gpu():
+    from paper_2112_13184_gb300 import ctm
+    with pytest.raises(ctm.CtmError) as e:
+        ctm.ctm_create(2, 2, ctm.ctm_default_options(chi=8, precision=ctm.CTM_OZAKI_INT8))
+    assert e.value.status == ctm.CTM_ERR_ARG
+    o = ctm.ctm_default_options(chi=8)
+    need = ctm.ctm_footprint_bytes(2, 2, o)
+    with pytest.raises(ctm.CtmError) as e:  # not 256-byte aligned
+        ctm.ctm_create_in(2, 2, o, 1, need)
+    assert e.value.status == ctm.CTM_ERR_ARG
+    with pytest.raises(ctm.CtmError) as e:  # smaller than the footprint
+        ctm.ctm_create_in(2, 2, o, 256, need - 1)
+    assert e.value.status == ctm.CTM_ERR_ARG
+
+
+def test_split_gemm_workspace_sizes():
+    from paper_2112_13184_gb300 import ctm
+    assert ctm.ctm_gemm_split_workspace_bytes(ctm.CTM_OZAKI_BF16, 64, 64, 64) == 0
+    assert ctm.ctm_gemm_split_workspace_bytes(ctm.CTM_SPLIT_BF16, 0, 64, 64) == 0
+    small = ctm.ctm_gemm_split_workspace_bytes(ctm.CTM_SPLIT_BF16, 200, 144, 1000)
+    big = ctm.ctm_gemm_split_workspace_bytes(ctm.CTM_SPLIT_BF16, 400, 144, 1000)
+    # three BF16 slices of both operands, padded rows: at least 2 s (M + N) K bytes
+    assert small >= 2 * 3 * (200 + 144) * 1000 and big > small
+    tf = ctm.ctm_gemm_split_workspace_bytes(ctm.CTM_3XTF32, 200, 144, 1000)
+    assert tf >= 4 * 2 * (200 + 144) * 1000  # two FP32-held TF32 slices
