@@ -310,7 +310,7 @@ def gate_leg(C, w, mixed, stream, slices):
             "gate_dE_le_1e-8": bool(dE.max() <= 1e-8)}
 
 
-def correlation_leg(C, w, solver, rmax=8, nev=4, block=8, max_iter=15):
+def correlation_leg(C, w, solver, rmax=8, nev=4, block=8, max_iter=25, tol=1e-8):
     """Sec. 5.3 on the solver's current environment (the gate leaves it at
     the mixed fixed point): <op1(r0) op1(r0 + r)> for r <= rmax along x and
     y from all four sites, and the leading transfer-matrix eigenvalues of
@@ -321,12 +321,12 @@ def correlation_leg(C, w, solver, rmax=8, nev=4, block=8, max_iter=15):
     t_corr = time.perf_counter() - t0
     cols = 2 * 4 * (3 * rmax + 2)
     t0 = time.perf_counter()
-    ratio, mod, e, it, ch, st = solver.transfer_spectrum(0, 0, nev=nev, block=block, max_iter=max_iter, tol=1e-10)
+    ratio, mod, e, it, ch, st = solver.transfer_spectrum(0, 0, nev=nev, block=block, max_iter=max_iter, tol=tol)
     t_tm = time.perf_counter() - t0
     return {"rmax": rmax, "seconds": t_corr, "column_contractions": cols, "ms_per_column": 1e3 * t_corr / cols,
             "C_x_site0": [float(x) for x in corr[0, 0]], "C_y_site0": [float(x) for x in corr[1, 0]],
             "transfer": {"seconds": t_tm, "cycles": it, "last_change": ch, "converged": st == C.CTM_OK,
-                         "block": block, "column_contractions": 2 * block * (32 // block) * it,
+                         "block": block, "tol": tol, "column_contractions": 2 * block * (32 // block) * it,
                          "abs_ratio": [float(x) for x in np.abs(ratio)], "e": [float(x) for x in e[1:]],
                          "xi_lattice_spacings": float(1.0 / e[1]) if e[1] > 0 else None}}
 
