@@ -146,6 +146,25 @@ ctm_status ctm_create(int Lx, int Ly, int d, int D, const ctm_options* opt, void
  * memory pool.) */
 ctm_status ctm_create_in(int Lx, int Ly, int d, int D, const ctm_options* opt, void* stream, void* arena,
                          size_t arena_bytes, ctm_handle* out);
+
+/* Device-memory pool of a serving loop: first-fit bookkeeping of offsets in
+ * one region of `bytes` the caller reserved once (host code only; the
+ * region itself is never touched).  Blocks are whole multiples of `grain`
+ * (a power of two; 256 for ctm_create_in) starting at multiples of it;
+ * freed blocks merge with free neighbours.  Thread-safe.  (No counterpart in
+ * the paper: the serving loop's memory pool.)
+ *   ctm_pool_alloc: *offset of a block of at least `bytes`, the first free
+ *     one that fits; CTM_ERR_OOM when none does.
+ *   ctm_pool_free: returns the block allocated at `offset` with the same
+ *     `bytes`; CTM_ERR_ARG for any other (offset, bytes), e.g. a second free.
+ *   ctm_pool_stats: bytes allocated, the largest free block, the number of
+ *     free blocks (each pointer optional). */
+typedef struct ctm_pool_s* ctm_pool;
+ctm_status ctm_pool_create(size_t bytes, size_t grain, ctm_pool* out);
+ctm_status ctm_pool_alloc(ctm_pool pool, size_t bytes, size_t* offset);
+ctm_status ctm_pool_free(ctm_pool pool, size_t offset, size_t bytes);
+ctm_status ctm_pool_stats(ctm_pool pool, size_t* used, size_t* largest_free, size_t* free_blocks);
+ctm_status ctm_pool_destroy(ctm_pool pool);
 ctm_status ctm_destroy(ctm_handle h);
 
 /* Copy in the site tensor A of site i (d*D^4 doubles, C-order [s,l,u,r,d]). */

@@ -17,7 +17,7 @@ INCLUDE = os.path.join(ROOT, "include")
 BUILD = os.path.join(ROOT, "_build")
 LIB = os.path.join(HERE, "libctm.so")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
-SOURCES = ["kernels.cu", "linalg.cu", "ozaki.cu", "engine.cu"]
+SOURCES = ["kernels.cu", "linalg.cu", "ozaki.cu", "engine.cu", "pool.cu"]
 
 
 def nvcc() -> str:

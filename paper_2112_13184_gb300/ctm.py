@@ -93,6 +93,11 @@ _sig("ctm_gemm_ozaki", c_int, c_int, c_int, c_int, c_int, c_int, c_double, c_voi
 _sig("ctm_svd_noalloc", c_int, c_void_p, c_int, c_void_p, c_void_p, c_void_p, c_void_p)
 _sig("ctm_create_in", c_int, c_int, c_int, c_int, c_int, ctypes.POINTER(ctm_options), c_void_p, c_void_p, c_size_t,
      c_void_p)
+_sig("ctm_pool_create", c_int, c_size_t, c_size_t, ctypes.POINTER(c_void_p))
+_sig("ctm_pool_alloc", c_int, c_void_p, c_size_t, ctypes.POINTER(c_size_t))
+_sig("ctm_pool_free", c_int, c_void_p, c_size_t, c_size_t)
+_sig("ctm_pool_stats", c_int, c_void_p, ctypes.POINTER(c_size_t), ctypes.POINTER(c_size_t), ctypes.POINTER(c_size_t))
+_sig("ctm_pool_destroy", c_int, c_void_p)
 _sig("ctm_correlation", c_int, c_void_p, c_void_p, c_void_p, c_int, c_void_p)
 _sig("ctm_transfer_spectrum", c_int, c_void_p, c_int, c_int, c_int, c_int, c_int, c_double, c_void_p,
      ctypes.POINTER(c_int), ctypes.POINTER(c_double))
@@ -236,6 +241,37 @@ def ctm_log_norm_per_site(h):
     v = c_double()
     _check(_lib.ctm_log_norm_per_site(h, ctypes.byref(v)), h)
     return v.value
+
+
+def ctm_pool_create(nbytes, grain):
+    p = c_void_p()
+    _check(_lib.ctm_pool_create(nbytes, grain, ctypes.byref(p)))
+    return p
+
+
+def ctm_pool_alloc(pool, nbytes):
+    """Offset of a block of at least nbytes, or None when no free block fits."""
+    off = c_size_t()
+    st = _lib.ctm_pool_alloc(pool, nbytes, ctypes.byref(off))
+    if st == CTM_ERR_OOM:
+        return None
+    _check(st)
+    return off.value
+
+
+def ctm_pool_free(pool, offset, nbytes):
+    _check(_lib.ctm_pool_free(pool, offset, nbytes))
+
+
+def ctm_pool_stats(pool):
+    """(bytes allocated, largest free block, number of free blocks)."""
+    u, l, n = c_size_t(), c_size_t(), c_size_t()
+    _check(_lib.ctm_pool_stats(pool, ctypes.byref(u), ctypes.byref(l), ctypes.byref(n)))
+    return u.value, l.value, n.value
+
+
+def ctm_pool_destroy(pool):
+    _check(_lib.ctm_pool_destroy(pool))
 
 
 def ctm_correlation(h, opA, opB, rmax):

@@ -7,7 +7,7 @@ convergence), and for one- and two-site expectation values (Sec. 5.3).
 
 Serving (continuous batching):
   * device memory: one region of `budget` bytes is reserved when the server
-    starts; a host-side first-fit pool hands each admitted request a block
+    starts; a first-fit pool (libctm's ctm_pool_*) hands each admitted request a block
     of its ctm_footprint_bytes, from which ctm_create_in carves the handle,
     so admission and retirement never call cudaMalloc / cudaFree (cudaFree
     waits for every stream on the device);
@@ -146,45 +146,37 @@ class CtmBackend:
 
 
 class DevicePool:
-    """First-fit allocator of offsets in one reserved region (blocks rounded
-    up to `grain` bytes -- 256 for device memory -- adjacent free blocks
-    merge)."""
+    """First-fit offsets in one reserved region, kept by libctm's native pool
+    (ctm_pool_*): blocks rounded up to `grain` bytes (256 for device memory),
+    freed neighbours merge, a second free of a block is refused."""
 
     def __init__(self, size: int, grain: int = 1):
+        from . import ctm
+        self._ctm = ctm
         self.size = int(size)
         self.grain = int(grain)
-        self.free: List[Tuple[int, int]] = [(0, self.size)]  # (offset, length), sorted
-
-    def _round(self, n: int) -> int:
-        return (int(n) + self.grain - 1) // self.grain * self.grain
+        self._p = ctm.ctm_pool_create(self.size, self.grain)
 
     def alloc(self, n: int) -> Optional[int]:
-        n = self._round(n)
-        for k, (o, ln) in enumerate(self.free):
-            if ln >= n:
-                if ln == n:
-                    self.free.pop(k)
-                else:
-                    self.free[k] = (o + n, ln - n)
-                return o
-        return None
+        return self._ctm.ctm_pool_alloc(self._p, int(n))
 
     def release(self, off: int, n: int) -> None:
-        n = self._round(n)
-        k = 0
-        while k < len(self.free) and self.free[k][0] < off:
-            k += 1
-        self.free.insert(k, (off, n))
-        merged: List[Tuple[int, int]] = []
-        for o, ln in self.free:
-            if merged and merged[-1][0] + merged[-1][1] == o:
-                merged[-1] = (merged[-1][0], merged[-1][1] + ln)
-            else:
-                merged.append((o, ln))
-        self.free = merged
+        self._ctm.ctm_pool_free(self._p, int(off), int(n))
 
     def largest(self) -> int:
-        return max((ln for _, ln in self.free), default=0)
+        return self._ctm.ctm_pool_stats(self._p)[1]
+
+    def stats(self) -> Tuple[int, int, int]:
+        """(bytes allocated, largest free block, number of free blocks)."""
+        return self._ctm.ctm_pool_stats(self._p)
+
+    def __del__(self):
+        try:
+            if self._p:
+                self._ctm.ctm_pool_destroy(self._p)
+                self._p = None
+        except Exception:
+            pass
 
 
 @dataclass

@@ -85,7 +85,7 @@ def test_first_fit_admission_respects_budget():
     assert fb.opened == [0, 2, 3, 1]
     assert sorted(r.rid for r in res) == [0, 1, 2, 3]
     assert all(r.converged for r in res)
-    assert fb.live == 0 and srv.in_use == 0 and srv.pool.free == [(0, 100)]  # pool merged back
+    assert fb.live == 0 and srv.in_use == 0 and srv.pool.stats() == (0, 100, 1)  # pool merged back
     for r in res:
         assert np.all(r.observables == r.rid)
 
@@ -119,16 +119,27 @@ def test_requests_advance_at_their_own_pace():
 
 
 def test_pool_first_fit_and_merge():
+    """The native pool: 256-byte granules, first fit, merging on free, and
+    no double free."""
+    from paper_2112_13184_gb300 import ctm
     from paper_2112_13184_gb300.serve import DevicePool
     p = DevicePool(1024, 256)
     a, b, c = p.alloc(100), p.alloc(300), p.alloc(200)
     assert (a, b, c) == (0, 256, 768) and p.alloc(10) is None  # 256-byte granules
+    assert p.stats() == (1024, 0, 0)
     p.release(b, 300)
-    assert p.alloc(256) == 256
+    assert p.alloc(256) == 256 and p.stats() == (768, 256, 1)
     p.release(a, 100)
     p.release(256, 256)
+    assert p.stats() == (256, 768, 1)  # [0, 768) merged
     p.release(c, 200)
-    assert p.free == [(0, 1024)]
+    assert p.stats() == (0, 1024, 1)
+    with pytest.raises(ctm.CtmError):
+        p.release(c, 200)  # second free
+    with pytest.raises(ctm.CtmError):
+        p.release(5, 256)  # not a block
+    with pytest.raises(ctm.CtmError):
+        DevicePool(1024, 100)  # grain not a power of two
 
 
 def test_stall_triggers_refinement():
